@@ -1,0 +1,225 @@
+"""Seeded synthetic workloads shaped like the test cases of arXiv 2102.12163.
+
+This module only describes problems: parameters and the exact cell averages of
+the initial conserved moments on the finest lattice.  It holds none of the
+method's arithmetic, and both the CUDA path and the CPU oracle take their
+inputs from it.
+
+Workloads (Section 5 of the paper for the shapes; the paper's own runs use
+Jmax = 9 and unstated boundary conditions):
+  advection  D1Q2, c = 0.75, lambda = 1, Omega = [-3, 3] periodic, indicator of
+             [-1, 1], Jmax = 10, T = 0.4 (Table 1 style, Test II-like)
+  burgers    D1Q2 Burgers, lambda = 1, Omega = [-3, 3] copy boundary, step of
+             height 0.5 plus three seeded Gaussian bumps, Jmax = 13, T = 1.0
+  shallow    vectorial D1Q2^2 shallow water, g = 1, lambda = 2, Omega = [-1, 1],
+             dam break h = 2 | 1, u = 0, Jmax = 15, T = 0.4
+  sod        vectorial D1Q2^3 Euler, gamma_gas = 1.4, lambda = 3, Omega = [-1, 1],
+             Sod tube, Jmax = 18, T = 0.4
+  batch      4096 seeded instances mixing the four families, Jmax in 8..14,
+             eps log-uniform in [1e-5, 1e-2], piecewise-constant data with
+             1..6 jumps, periodic.
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field, replace
+
+import numpy as np
+
+EQ_ADVECTION, EQ_BURGERS, EQ_SW, EQ_EULER = 0, 1, 2, 3
+NFIELDS = {EQ_ADVECTION: 1, EQ_BURGERS: 1, EQ_SW: 2, EQ_EULER: 3}
+BC_PERIODIC, BC_COPY = 0, 1
+GAMMA_GAS = 1.4
+
+
+@dataclass
+class Instance:
+    """One 1D problem: scheme, multiresolution parameters and initial data."""
+
+    name: str
+    eq: int
+    Jmin: int
+    Jmax: int
+    eps: float
+    lam: float
+    a: float
+    b: float
+    bc: int
+    T: float
+    gamma: int = 1
+    mu_bar: int = 0
+    s: tuple = (1.0, 1.0, 1.0)
+    eqp: float = 0.0  # advection velocity | unused | gravity | gas constant
+    m0: np.ndarray = field(default=None, repr=False)  # (nf, 2^Jmax) cell averages
+
+    @property
+    def nf(self) -> int:
+        return NFIELDS[self.eq]
+
+    @property
+    def q(self) -> int:
+        return 2 * self.nf
+
+    @property
+    def dx(self) -> float:
+        return (self.b - self.a) / (1 << self.Jmax)
+
+    @property
+    def nsteps(self) -> int:
+        """N = T / dt with dt = dx / lambda (acoustic scaling), nearest integer."""
+        return int(round(self.T * self.lam / self.dx))
+
+    def with_(self, **kw) -> "Instance":
+        return replace(self, **kw)
+
+
+# exact cell averages ---------------------------------------------------------
+
+def cell_edges(a: float, b: float, J: int) -> np.ndarray:
+    n = 1 << J
+    return a + (b - a) * np.arange(n + 1, dtype=np.float64) / n
+
+
+def avg_indicator(edges: np.ndarray, lo: float, hi: float) -> np.ndarray:
+    """Average of the indicator of [lo, hi] over each cell (overlap length / dx)."""
+    left, right = edges[:-1], edges[1:]
+    ov = np.clip(np.minimum(right, hi) - np.maximum(left, lo), 0.0, None)
+    return ov / (right - left)
+
+
+def avg_gaussian(edges: np.ndarray, amp: float, x0: float, w: float) -> np.ndarray:
+    """Average of amp * exp(-(x - x0)^2 / (2 w^2)) over each cell, via erf."""
+    from scipy.special import erf
+
+    z = (edges - x0) / (math.sqrt(2.0) * w)
+    prim = amp * w * math.sqrt(math.pi / 2.0) * erf(z)
+    return np.diff(prim) / np.diff(edges)
+
+
+def avg_piecewise(edges: np.ndarray, jumps: np.ndarray, values: np.ndarray) -> np.ndarray:
+    """Average of a piecewise-constant function: values[i] on (jumps[i-1], jumps[i])."""
+    bounds = np.concatenate([[edges[0]], np.sort(jumps), [edges[-1]]])
+    out = np.zeros(edges.size - 1)
+    for i, v in enumerate(values):
+        out += v * avg_indicator(edges, bounds[i], bounds[i + 1])
+    return out
+
+
+# the named workloads ---------------------------------------------------------
+
+def advection(Jmax: int = 10, eps: float = 1e-4, c: float = 0.75, s: float = 1.0,
+              lo: float = -1.0, hi: float = 1.0, T: float = 0.4, Jmin: int = 2) -> Instance:
+    inst = Instance("advection", EQ_ADVECTION, Jmin, Jmax, eps, 1.0, -3.0, 3.0, BC_PERIODIC, T,
+                    s=(s,), eqp=c)
+    inst.m0 = avg_indicator(cell_edges(inst.a, inst.b, Jmax), lo, hi)[None, :]
+    return inst
+
+
+def burgers(Jmax: int = 13, eps: float = 1e-4, seed: int = 2102, T: float = 1.0, s: float = 1.0,
+            Jmin: int = 2) -> Instance:
+    rng = np.random.Generator(np.random.PCG64(seed))
+    xs = rng.uniform(-0.5, 0.5)
+    amp = rng.uniform(0.05, 0.15, 3)
+    x0 = rng.uniform(-2.5, 2.5, 3)
+    w = rng.uniform(0.05, 0.2, 3)
+    inst = Instance("burgers", EQ_BURGERS, Jmin, Jmax, eps, 1.0, -3.0, 3.0, BC_COPY, T, s=(s,))
+    e = cell_edges(inst.a, inst.b, Jmax)
+    rho = 0.5 * avg_indicator(e, inst.a - 1.0, xs)
+    for i in range(3):
+        rho = rho + avg_gaussian(e, amp[i], x0[i], w[i])
+    inst.m0 = rho[None, :]
+    return inst
+
+
+def shallow_water(Jmax: int = 15, eps: float = 1e-4, T: float = 0.4, g: float = 1.0,
+                  s: float = 1.0, Jmin: int = 2) -> Instance:
+    inst = Instance("shallow", EQ_SW, Jmin, Jmax, eps, 2.0, -1.0, 1.0, BC_COPY, T,
+                    s=(s, s), eqp=g)
+    e = cell_edges(inst.a, inst.b, Jmax)
+    h = 2.0 * avg_indicator(e, -1.0, 0.0) + 1.0 * avg_indicator(e, 0.0, 1.0)
+    inst.m0 = np.stack([h, np.zeros_like(h)])
+    return inst
+
+
+def sod(Jmax: int = 18, eps: float = 1e-4, T: float = 0.4, s: float = 1.0, Jmin: int = 2) -> Instance:
+    inst = Instance("sod", EQ_EULER, Jmin, Jmax, eps, 3.0, -1.0, 1.0, BC_COPY, T,
+                    s=(s, s, s), eqp=GAMMA_GAS)
+    e = cell_edges(inst.a, inst.b, Jmax)
+    left, right = avg_indicator(e, -1.0, 0.0), avg_indicator(e, 0.0, 1.0)
+    rho = 1.0 * left + 0.125 * right
+    E = 2.5 * left + 0.25 * right
+    inst.m0 = np.stack([rho, np.zeros_like(rho), E])
+    return inst
+
+
+def batch(n: int = 4096, seed: int = 12163, Jmin: int = 2, Jmax_range=(8, 14),
+          eps_log10=(-5.0, -2.0)) -> list[Instance]:
+    """Mixed batch of independent periodic instances with piecewise-constant data."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    out = []
+    for i in range(n):
+        fam = int(rng.integers(0, 4))
+        J = int(rng.integers(Jmax_range[0], Jmax_range[1] + 1))
+        eps = float(10.0 ** rng.uniform(*eps_log10))
+        nj = int(rng.integers(1, 7))
+        jumps = np.sort(rng.uniform(-1.0, 1.0, nj))
+        e = cell_edges(-1.0, 1.0, J)
+        if fam == EQ_ADVECTION or fam == EQ_BURGERS:
+            vals = rng.uniform(-0.9, 0.9, nj + 1)
+            c = float(rng.uniform(-0.9, 0.9)) if fam == EQ_ADVECTION else 0.0
+            inst = Instance(f"b{i}", fam, Jmin, J, eps, 1.0, -1.0, 1.0, BC_PERIODIC, 0.0,
+                            s=(1.0,), eqp=c)
+            inst.m0 = avg_piecewise(e, jumps, vals)[None, :]
+        elif fam == EQ_SW:
+            h = rng.uniform(0.5, 2.0, nj + 1)
+            inst = Instance(f"b{i}", fam, Jmin, J, eps, 2.0, -1.0, 1.0, BC_PERIODIC, 0.0,
+                            s=(1.0, 1.0), eqp=1.0)
+            hh = avg_piecewise(e, jumps, h)
+            inst.m0 = np.stack([hh, np.zeros_like(hh)])
+        else:
+            rho = rng.uniform(0.4, 1.0, nj + 1)
+            p = rng.uniform(0.1, 1.0, nj + 1)
+            inst = Instance(f"b{i}", fam, Jmin, J, eps, 3.0, -1.0, 1.0, BC_PERIODIC, 0.0,
+                            s=(1.0, 1.0, 1.0), eqp=GAMMA_GAS)
+            rr = avg_piecewise(e, jumps, rho)
+            EE = avg_piecewise(e, jumps, p / (GAMMA_GAS - 1.0))
+            inst.m0 = np.stack([rr, np.zeros_like(rr), EE])
+        out.append(inst)
+    return out
+
+
+def random_smooth(Jmax: int, eq: int, seed: int, Jmin: int = 2, eps: float = 1e-3, bc: int = BC_PERIODIC,
+                  nmodes: int = 3) -> Instance:
+    """Small seeded instance with smooth plus step data, for parity tests."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    lam = {EQ_ADVECTION: 1.0, EQ_BURGERS: 1.0, EQ_SW: 2.0, EQ_EULER: 3.0}[eq]
+    nf = NFIELDS[eq]
+    inst = Instance(f"rand{seed}", eq, Jmin, Jmax, eps, lam, -1.0, 1.0, bc, 0.0,
+                    s=tuple(float(v) for v in rng.uniform(0.8, 1.6, 3)),
+                    eqp={EQ_ADVECTION: float(rng.uniform(-0.9, 0.9)), EQ_BURGERS: 0.0,
+                         EQ_SW: 1.0, EQ_EULER: GAMMA_GAS}[eq])
+    e = cell_edges(-1.0, 1.0, Jmax)
+    xs = float(rng.uniform(-0.5, 0.5))
+    base = avg_indicator(e, -1.0, xs)
+    bumps = np.zeros(e.size - 1)
+    for _ in range(nmodes):
+        bumps = bumps + avg_gaussian(e, float(rng.uniform(0.02, 0.1)), float(rng.uniform(-0.8, 0.8)),
+                                     float(rng.uniform(0.03, 0.2)))
+    if eq in (EQ_ADVECTION, EQ_BURGERS):
+        inst.m0 = (0.5 * base + bumps - 0.2)[None, :]
+    elif eq == EQ_SW:
+        h = 1.0 + 0.8 * base + bumps
+        inst.m0 = np.stack([h, 0.1 * bumps])
+    else:
+        rho = 0.5 + 0.4 * base + bumps
+        p = 0.3 + 0.5 * base
+        inst.m0 = np.stack([rho, 0.05 * bumps, p / (GAMMA_GAS - 1.0)])
+    return inst
+
+
+CONFIGS = {
+    "advection": advection,
+    "burgers": burgers,
+    "shallow": shallow_water,
+    "sod": sod,
+}
