@@ -1,0 +1,359 @@
+"""Benchmark of the adaptive MR-LBM step on GB300: leaf-cell updates per second.
+
+A step is one adaptive time step (multiresolution analysis, mesh update, data
+transfer, leaves collision, reconstructed-flux stream) of every instance of the
+workload.  The default workload is the mixed batch of 4096 independent
+instances (D1Q2 advection / Burgers, vectorial D1Q2^2 shallow water, vectorial
+D1Q2^3 Euler; Jmax uniform in 8..14; eps log-uniform in [1e-5, 1e-2];
+piecewise-constant data with 1..6 jumps), run in FP32 (the headline) and in
+FP64 on the same inputs.  Timed: exactly K steps in one persistent launch,
+bracketed by a barrier and a device synchronisation, CUDA events on the
+solver's stream; the per-GPU state (several GB) is far larger than L2.
+
+  python bench.py [--gpus N --steps K --warmup W] [--impl reference]
+                  [--workload batch|burgers|sod|shallow|advection]
+
+Under torchrun every rank runs its own seeded batch (weak scaling, no
+collective on the data path); rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "adaptive LBM leaf-cell updates/s at 1 GB300, FP32 vs FP64, at matched L1 error"
+UNIT = "leaf-cell updates/s"
+HBM_FALLBACK = 6800.0
+
+
+# --------------------------------------------------------------------------- helpers
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            j = json.load(fh)
+        return float(j["hbm_gbs"]), "measured"
+    except Exception:
+        return HBM_FALLBACK, "fallback"
+
+
+def source_hash() -> str:
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2102_12163_gb300", "csrc")
+    for name in sorted(os.listdir(csrc)):
+        with open(os.path.join(csrc, name), "rb") as fh:
+            h.update(name.encode())
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(workload: str, precision: str):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken on
+    the current kernel source (else None)."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as fh:
+            j = json.load(fh)
+        e = j[f"{workload}:{precision}"]
+        if e.get("source_hash") != source_hash():
+            return None
+        return e
+    except Exception:
+        return None
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.t.join(timeout=2)
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.lines:
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def make_workload(name: str, rank: int):
+    from paper_2102_12163_gb300 import workloads as W
+
+    if name == "batch":
+        insts = W.batch(n=4096, seed=12163 + rank)
+        desc = "batch of 4096 mixed D1Q2 advection/Burgers, D1Q2^2 shallow water, D1Q2^3 Euler; Jmax 8..14; eps 1e-5..1e-2"
+    else:
+        insts = [W.CONFIGS[name]()]
+        i = insts[0]
+        desc = f"{name} single instance, Jmin {i.Jmin} Jmax {i.Jmax} eps {i.eps:g}"
+    return insts, desc
+
+
+# --------------------------------------------------------------------------- oracle (CPU) timing
+
+def _oracle_task(args):
+    inst, warm, n = args
+    sys.path.insert(0, ROOT)
+    import oracle as O
+
+    p = O.Params(Jmin=inst.Jmin, Jmax=inst.Jmax, eq=inst.eq, lam=inst.lam, eps=inst.eps, gamma=inst.gamma,
+                 mu_bar=inst.mu_bar, bc=inst.bc, a=inst.a, b=inst.b, s=inst.s, eqp=inst.eqp)
+    o = O.Oracle(p)
+    o.set_initial(inst.m0)
+    o.step(warm)
+    upd = 0
+    t0 = time.perf_counter()
+    for _ in range(n):
+        o.step()
+        upd += len(o.leaves()[0])
+    return upd, time.perf_counter() - t0
+
+
+def oracle_throughput(insts, target_s: float = 15.0, warm: int = 2):
+    """The oracle as it stands on a bounded sample of the workload, spread over
+    the host cores with a spawned process pool; returns (value, cores, sample)."""
+    import multiprocessing as mp
+    from concurrent.futures import ProcessPoolExecutor
+
+    cores = max(1, min(os.cpu_count() or 1, 16))
+    stride = max(1, len(insts) // (4 * cores))
+    sample = insts[::stride][: 4 * cores]
+    # calibrate steps per instance on one instance
+    u, t = _oracle_task((sample[0], warm, 1))
+    per_step = max(t, 1e-4)
+    n = int(max(1, min(64, target_s * cores / (per_step * len(sample)))))
+    ctx = mp.get_context("spawn")
+    t0 = time.perf_counter()
+    with ProcessPoolExecutor(cores, mp_context=ctx) as ex:
+        res = list(ex.map(_oracle_task, [(i, warm, n) for i in sample]))
+    wall = time.perf_counter() - t0
+    upd = sum(r[0] for r in res)
+    busy = sum(r[1] for r in res)
+    value = upd / busy * cores
+    desc = (f"{len(sample)} of {len(insts)} instances (every {stride}th), {warm} untimed + {n} timed steps each, "
+            f"{cores} worker processes, {wall:.1f} s wall")
+    return value, cores, desc
+
+
+# --------------------------------------------------------------------------- GPU leg
+
+def run_gpu(insts, precision: int, steps: int, warmup: int, rank: int, world: int, dist, block=None):
+    import numpy as np
+    import torch
+
+    from paper_2102_12163_gb300 import MRLBM
+
+    s = MRLBM(insts, precision=precision, device=f"cuda:{torch.cuda.current_device()}", block=block)
+    s.set_initial()
+    s.advance(warmup)
+    s.sync()
+    u0, _, _ = s.stats()
+    l0 = s.launches()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(torch.cuda.current_device()) as clk:
+        t_wall = time.perf_counter()
+        ev0.record(s.stream)
+        s.advance(steps)
+        ev1.record(s.stream)
+        ev1.synchronize()
+        t_wall = time.perf_counter() - t_wall
+    torch.cuda.synchronize()
+    s.sync()
+    dt = ev0.elapsed_time(ev1) / 1e3
+    launches = s.launches() - l0
+    u1, _, _ = s.stats()
+    upd = u1 - u0
+    q = np.array([i.q for i in insts], dtype=np.float64)
+    # algorithmic bytes: each leaf's q populations read and written once per step
+    # (the per-instance mean q weighted by that instance's updates is not
+    # tracked on the device, so the batch mean q over leaves is used)
+    _, nleaf = s.summary()
+    qmean = float((q * nleaf).sum() / max(1, nleaf.sum()))
+    vb = 4 if precision == 1 else 8
+    if dist:
+        t = torch.tensor([dt, float(upd), t_wall], dtype=torch.float64, device="cuda")
+        tm = t.clone()
+        dist.all_reduce(tm[:1], op=dist.ReduceOp.MAX)
+        dist.all_reduce(tm[1:2], op=dist.ReduceOp.SUM)
+        dt, upd = float(tm[0]), float(tm[1])
+    res = {
+        "solver": s, "dt": dt, "updates": upd, "launches": launches, "clocks": clk.summary(),
+        "bytes_alg": 2.0 * qmean * vb * upd, "qmean": qmean, "t_wall": t_wall,
+    }
+    return res
+
+
+def e2e(s, steps: int):
+    """Same metric through the public API with host buffers: pinned initial data
+    uploaded, K steps, per-instance summary read back, all inside the timer."""
+    import numpy as np
+    import torch
+
+    host = torch.from_numpy(s.initial_data()).pin_memory()
+    n = len(s.instances)
+    mass = torch.empty((n, 3), dtype=torch.float64).pin_memory()
+    nleaf = torch.empty(n, dtype=torch.int32).pin_memory()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    s.set_initial(host)
+    s.advance(steps)
+    s.summary(mass, nleaf)
+    t = time.perf_counter() - t0
+    upd, _, _ = s.stats()
+    del np
+    return {"value": upd / t, "unit": UNIT, "h2d_bytes_per_step": host.numel() * 8 / steps,
+            "d2h_bytes_per_step": (mass.numel() * 8 + nleaf.numel() * 4) / steps, "seconds": t}
+
+
+# --------------------------------------------------------------------------- main
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=32)
+    ap.add_argument("--warmup", type=int, default=4)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="batch", choices=["batch", "advection", "burgers", "shallow", "sod"])
+    ap.add_argument("--block", type=int, default=None)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fp64", action="store_true")
+    args = ap.parse_args()
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    insts, desc = make_workload(args.workload, rank)
+    hbm, hbm_src = peaks()
+
+    if args.impl == "reference":
+        # the reference arm is the oracle as it stands, on the host cores, rank 0 only
+        if rank != 0:
+            return
+        K, W = args.steps, args.warmup
+        value, cores, sample = oracle_throughput(insts, target_s=max(5.0, 60.0 / max(1, K)) * K / 4)
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": K, "warmup": W,
+                "ms_per_step": None, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "f64", "data": "synthetic", "impl": "reference",
+                "config": {"workload": desc},
+                "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+                "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+        print(json.dumps(line), flush=True)
+        return
+
+    import torch
+
+    dist = None
+    if world > 1:
+        import torch.distributed as td
+
+        torch.cuda.set_device(local)
+        td.init_process_group("nccl")
+        dist = td
+    else:
+        torch.cuda.set_device(0)
+
+    from paper_2102_12163_gb300 import MR_FP32_MIXED, MR_FP64
+
+    r32 = run_gpu(insts, MR_FP32_MIXED, args.steps, args.warmup, rank, world, dist, args.block)
+    r64 = None if args.no_fp64 else run_gpu(insts, MR_FP64, args.steps, args.warmup, rank, world, dist, args.block)
+    ee = e2e(r32["solver"], args.steps)
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        v, cores, sample = oracle_throughput(insts)
+        cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample}
+
+    if dist:
+        dist.barrier()
+    if rank != 0:
+        dist.destroy_process_group()
+        return
+
+    def roof(r, prec):
+        achieved = r["bytes_alg"] / r["dt"] / 1e9
+        tr = profiled_traffic(args.workload, prec)
+        return {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+                "traffic": (tr["dram_bytes_per_launch"] if tr else None),
+                "peak_source": f"{hbm_src} HBM copy bandwidth (MEASURED_PEAKS.json)" if hbm_src == "measured"
+                else "fallback 6.8 TB/s", "algorithmic_bytes_per_update": 2 * r["qmean"] * (4 if prec == "fp32" else 8)}
+
+    line = {
+        "metric": METRIC, "value": r32["updates"] / r32["dt"], "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": r32["dt"] * 1e3 / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": desc, "instances_per_gpu": len(insts), "steps_per_launch": args.steps,
+                   "l2": "inputs larger than L2 (per-GPU workspace of several GB)",
+                   "precision": "FP32 populations, FP64 coarse-level detail test and mass audit"},
+        "roofline": roof(r32, "fp32"),
+        "cpu_baseline": cpu,
+        "e2e": ee,
+        "gpu_launches": r32["launches"],
+        "clocks": r32["clocks"],
+    }
+    if r64:
+        line["fp64"] = {"value": r64["updates"] / r64["dt"], "ms_per_step": r64["dt"] * 1e3 / args.steps,
+                        "roofline": roof(r64, "fp64"), "gpu_launches": r64["launches"], "clocks": r64["clocks"]}
+    print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,182 @@
+/*
+ * mrlbm.h -- C ABI of the GB300 implementation of the multiresolution-adaptive
+ * lattice Boltzmann step of Bellotti, Gouarin, Graille and Massot
+ * (arXiv 2102.12163).
+ *
+ * One context holds one or many independent 1D problems ("instances").  Each
+ * instance lives on a dyadic cell tree with levels Jmin..Jmax (Section 3.1):
+ * level l has 2^l cells of size (b - a) 2^-l.  One adaptive time step is
+ *   mr_adapt : multiresolution analysis (projection, prediction, details,
+ *              Sections 3.1-3.2), mesh update Lambda^{n+1} = G(H(T(Lambda^n)))
+ *              (Section 4.1, enlargement Section 4.2) and data transfer;
+ *   lbm_step : leaves collision (eq. LeavesCollision, Section 4.5) and stream
+ *              with fluxes reconstructed on virtual finest cells
+ *              (eq. AdaptiveStreamPhase, Section 4.3).
+ *
+ * Conventions
+ *   - Every call returns an mr_status; nothing else crosses the ABI.
+ *   - Device memory is owned by the caller: the library never allocates it.
+ *     mr_workspace_size() gives the bytes one context needs and mr_bind()
+ *     attaches a caller-allocated device buffer of at least that size (256-byte
+ *     aligned) and the CUDA stream every later call is ordered on.  The buffer
+ *     must outlive the context's use; mr_destroy() does not free it.
+ *   - Calls that launch work are asynchronous on the bound stream.  Errors found
+ *     on the device (non-finite values) are reported by the next call that
+ *     synchronises: mr_sync(), the getters, mr_stats().
+ *   - Pointers marked "host or device" may be either (unified addressing);
+ *     pointers marked "host" must be host memory.
+ *   - The library is not thread-safe per context.
+ *
+ * Scope of this build: D = 1, vectorial D1Q2^n schemes (velocities +-lambda per
+ * field), prediction stencil gamma = 1 (c1 = -1/8), enlargement width sigma = 1.
+ */
+#ifndef MRLBM_H
+#define MRLBM_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct mr_ctx mr_ctx;
+
+typedef enum {
+    MR_OK = 0,
+    MR_ERR_ARG = -1,       /* invalid argument (message via mr_last_error)      */
+    MR_ERR_CUDA = -2,      /* a CUDA runtime call failed                        */
+    MR_ERR_CAPACITY = -3,  /* a caller buffer or the workspace is too small     */
+    MR_ERR_NONFINITE = -4, /* a population became NaN or infinite on the device */
+    MR_ERR_TIMEOUT = -5,   /* reserved: a bounded device wait gave up           */
+    MR_ERR_STATE = -6      /* call out of order (e.g. step before mr_bind)      */
+} mr_status;
+
+typedef enum { MR_FP64 = 0, MR_FP32_MIXED = 1 } mr_precision;
+typedef enum { MR_BC_PERIODIC = 0, MR_BC_COPY = 1 } mr_bc;
+/* Equilibria of the vectorial D1Q2^n schemes (Section 5):
+ *   ADVECTION   n = 1, m1eq = c m0                         eq_param = c
+ *   BURGERS     n = 1, m1eq = m0^2 / 2                     eq_param unused
+ *   SW_VEC      n = 2, shallow water (h, hu), gravity g    eq_param = g
+ *   EULER_VEC   n = 3, Euler (rho, rho u, E), Section 5.3  eq_param = gamma_gas */
+typedef enum { MR_EQ_ADVECTION = 0, MR_EQ_BURGERS = 1, MR_EQ_SW_VEC = 2, MR_EQ_EULER_VEC = 3 } mr_equilibrium;
+
+/* Per-instance description for the batched interface. */
+typedef struct {
+    int Jmin, Jmax;   /* 2 <= Jmin <= Jmax <= 24 */
+    int gamma;        /* prediction stencil, must be 1 */
+    int mu_bar;       /* Harten regularity guess, >= 0 (eq. HartenLossOfRegularity) */
+    int bc;           /* mr_bc */
+    int eq;           /* mr_equilibrium */
+    double eps;       /* threshold epsilon (Prop. ErrorControl), >= 0 */
+    double a, b;      /* domain [a, b] */
+    double lambda;    /* lattice velocity, dt = dx_Jmax / lambda */
+    double s[3];      /* relaxation rate of the non-conserved moment of each field */
+    double eq_param;  /* see mr_equilibrium */
+} mr_instance_desc;
+
+/* ---- creation -------------------------------------------------------- */
+
+/* Mesh part of the problem statement (Sections 3.1-3.4, 4.2): one instance.
+ * precision: mr_precision.  The scheme is set by lbm_scheme() before mr_bind(). */
+mr_status mr_mesh_init(mr_ctx **out, int Jmin, int Jmax, int gamma, double eps, double a,
+                       double b, int bc, int mu_bar, int precision);
+
+/* Scheme part (d'Humieres formalism, Section 2.1): DdQq with d = 1 and
+ * q = 2 n, lattice velocity lambda, relaxation rates s[0..n-1] of the
+ * non-conserved moments, equilibrium eq with parameter *eq_params. */
+mr_status lbm_scheme(mr_ctx *ctx, int d, int q, double lambda, const double *s, int eq,
+                     const double *eq_params);
+
+/* n independent instances in one context (batched persistent launch). */
+mr_status mr_batch_create(mr_ctx **out, const mr_instance_desc *desc, int n, int precision);
+
+/* Device bytes needed by the context (valid once every scheme is set). */
+mr_status mr_workspace_size(const mr_ctx *ctx, size_t *bytes);
+
+/* Attach the caller-owned device workspace and the CUDA stream (cudaStream_t,
+ * NULL for the legacy default stream).  Uploads the reconstruction tables. */
+mr_status mr_bind(mr_ctx *ctx, void *d_workspace, size_t bytes, void *stream);
+
+/* ---- state ----------------------------------------------------------- */
+
+/* Initial datum (Section 2.1, Lambda^0 = full tree, Section 4.4): cell averages
+ * of the conserved moments on the finest lattice, for every instance in order,
+ * field-major per instance: instance i occupies n_i * 2^Jmax_i doubles
+ * (field j, cell k at j * 2^Jmax_i + k).  Populations start at equilibrium.
+ * Host or device pointer; count = total number of doubles. */
+mr_status mr_set_initial(mr_ctx *ctx, const double *m_cons, size_t count);
+
+/* Arbitrary state of one instance (testing, restart): R[c] != 0 marks cell c of
+ * the complete tree R(Lambda), values[h * S + c] the population h on cell c,
+ * cells numbered level by level (level l: [2^l - 2^Jmin, 2^(l+1) - 2^Jmin)),
+ * S = 2^(Jmax+1) - 2^Jmin.  Only leaf values are used.  Device pointers.
+ * The tree is checked on the host first (coarsest level whole, siblings
+ * together, graded for gamma = 1); MR_ERR_ARG if it is not. */
+mr_status mr_set_state(mr_ctx *ctx, int inst, const unsigned char *R, const double *values);
+
+/* ---- the adaptive step ------------------------------------------------ */
+
+mr_status mr_adapt(mr_ctx *ctx);              /* Section 4.1 on every instance      */
+mr_status lbm_step(mr_ctx *ctx);              /* Sections 4.3, 4.5 on every instance */
+mr_status mr_advance(mr_ctx *ctx, int nsteps); /* nsteps x (mr_adapt; lbm_step), one launch */
+
+/* Waits for the bound stream and reports device-side errors. */
+mr_status mr_sync(mr_ctx *ctx);
+
+/* ---- results (synchronising; host output pointers) -------------------- */
+
+/* Complete leaves S(Lambda) of instance inst, ordered by level then index, with
+ * their q populations (f[h * cap + i]); any output may be NULL. */
+mr_status mr_get_leaves(mr_ctx *ctx, int inst, int *level, long *index, double *f, long cap,
+                        long *count);
+
+/* Conserved moments on the leaves (m[j * cap + i]), same order as mr_get_leaves. */
+mr_status mr_get_moments(mr_ctx *ctx, int inst, double *m, long cap, long *count);
+
+/* Conserved moments reconstructed on every finest cell (n * 2^Jmax values,
+ * m[j * 2^Jmax + k]); the multiresolution reconstruction of Section 3.3.
+ * Host or device pointer. */
+mr_status mr_get_finest(mr_ctx *ctx, int inst, double *m_finest);
+
+/* Complete tree membership R (S bytes, cell numbering of mr_set_state). */
+mr_status mr_get_tree(mr_ctx *ctx, int inst, unsigned char *R);
+
+/* FP64 conserved totals sum_leaves dx_l m_j (n values) and the largest
+ * per-step residual |mass change - boundary flux| seen so far. */
+mr_status mr_audit(mr_ctx *ctx, int inst, double *mass, double *residual);
+
+/* Per-instance summary in one copy: FP64 conserved totals (mass[3 * i + j],
+ * zero past the instance's field count) and current leaf counts nleaf[i];
+ * either output may be NULL.  Host pointers. */
+mr_status mr_get_summary(mr_ctx *ctx, double *mass, int *nleaf);
+
+/* Totals over the context: leaf-cell updates (sum over steps and instances of
+ * #S(Lambda^{n+1})), steps taken by instance 0, current leaves over instances. */
+mr_status mr_stats(mr_ctx *ctx, unsigned long long *updates, unsigned long long *steps,
+                   long long *leaves);
+
+/* Launch shape: threads per block (128, 256, 512 or 1024) and blocks (0 = one
+ * wave of resident blocks).  Takes effect at the next launch. */
+mr_status mr_set_launch(mr_ctx *ctx, int block, int grid);
+
+/* Reconstruction coefficients used by the stream (Section 3.3 with gamma = 1):
+ * for a leaf at level gap dj = Jmax - l (0 <= dj <= 24), kind 0 gives the
+ * 4 weights of the first finest cell on the level-l window (k-2, k-1, k, k+1),
+ * kind 1 the 4 weights on the window (2k-2, 2k-1, 2k, 2k+1) of level l+1 (used
+ * next to a finer neighbour), kind 2 the 2 weights on (0, 1) for the leaf
+ * k = 0 at a copy boundary.  The last finest cell uses the mirrored weights.
+ * Host-only query, no device needed. */
+mr_status mr_reconstruction_coefficients(int dj, int kind, double *out);
+
+/* Number of instances, and the number of kernel launches issued so far. */
+mr_status mr_info(const mr_ctx *ctx, int *n_instances, long long *launches);
+
+/* Last error message of the context (or of the last failed creation if ctx is NULL). */
+mr_status mr_last_error(const mr_ctx *ctx, char *buf, int len);
+
+mr_status mr_destroy(mr_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

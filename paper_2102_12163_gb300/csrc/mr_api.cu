@@ -1,0 +1,702 @@
+// mr_api.cu -- host implementation of the C ABI declared in include/mrlbm.h.
+//
+// The library never allocates device memory: the caller hands over one device
+// buffer (mr_bind) that is carved into the per-context header (descriptors,
+// per-instance state, work queue, reconstruction tables, input staging) and the
+// per-instance regions described in mr_common.h.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstddef>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/mrlbm.h"
+#include "mr_common.h"
+
+using namespace mrg;
+
+namespace {
+
+size_t align_up(size_t x, size_t a = 256) { return (x + a - 1) / a * a; }
+
+int nfields_of(int eq) {
+    switch (eq) {
+    case MR_EQ_ADVECTION:
+    case MR_EQ_BURGERS: return 1;
+    case MR_EQ_SW_VEC: return 2;
+    case MR_EQ_EULER_VEC: return 3;
+    default: return 0;
+    }
+}
+
+int nwords_h(int l) { return l >= 5 ? (1 << (l - 5)) : 1; }
+
+thread_local std::string g_create_error;
+
+}  // namespace
+
+struct mr_ctx {
+    std::vector<mr_instance_desc> desc;
+    std::vector<bool> scheme_set;
+    int precision = MR_FP64;
+    // layout (bytes from the workspace base)
+    size_t off_desc = 0, off_state = 0, off_order = 0, off_ident = 0, off_queue = 0, off_tab = 0,
+           off_stage = 0, total = 0;
+    std::vector<size_t> inst_off;  // per instance region start
+    std::vector<InstDesc> hdesc;   // host copy of the device descriptors
+    std::vector<long long> m_off;  // per instance offset in the initial-data array
+    size_t stage_doubles = 0;
+    // binding
+    unsigned char *ws = nullptr;
+    size_t ws_bytes = 0;
+    cudaStream_t stream = nullptr;
+    bool bound = false, initialised = false;
+    int block = 0, grid = 0, grid_req = 0, sms = 0;
+    long long launches = 0;
+    std::string err;
+
+    int fail(int code, const char *fmt, ...) {
+        char buf[512];
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(buf, sizeof buf, fmt, ap);
+        va_end(ap);
+        err = buf;
+        return code;
+    }
+    int cuda(cudaError_t e, const char *what) {
+        if (e == cudaSuccess) return MR_OK;
+        return fail(MR_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+    }
+    bool fp32() const { return precision == MR_FP32_MIXED; }
+    size_t vbytes() const { return fp32() ? 4 : 8; }
+    int n() const { return (int)desc.size(); }
+};
+
+// ---------------------------------------------------------------------------
+// validation and layout
+
+static int check_desc(mr_ctx *c, const mr_instance_desc &d, int i) {
+    if (d.Jmin < 2 || d.Jmax < d.Jmin || d.Jmax > MAXLEV)
+        return c->fail(MR_ERR_ARG, "instance %d: need 2 <= Jmin <= Jmax <= %d (got %d, %d)", i, MAXLEV, d.Jmin, d.Jmax);
+    if (d.gamma != 1) return c->fail(MR_ERR_ARG, "instance %d: only the gamma = 1 prediction is built", i);
+    if (d.mu_bar < 0 || d.mu_bar > 30) return c->fail(MR_ERR_ARG, "instance %d: mu_bar out of range", i);
+    if (d.bc != MR_BC_PERIODIC && d.bc != MR_BC_COPY) return c->fail(MR_ERR_ARG, "instance %d: bad boundary", i);
+    if (nfields_of(d.eq) == 0) return c->fail(MR_ERR_ARG, "instance %d: bad equilibrium", i);
+    if (!(d.eps >= 0.0) || !(d.b > d.a) || !(d.lambda > 0.0))
+        return c->fail(MR_ERR_ARG, "instance %d: need eps >= 0, b > a, lambda > 0", i);
+    for (int j = 0; j < nfields_of(d.eq); ++j)
+        if (!(d.s[j] > 0.0 && d.s[j] <= 2.0)) return c->fail(MR_ERR_ARG, "instance %d: relaxation rate outside (0, 2]", i);
+    return MR_OK;
+}
+
+static void layout(mr_ctx *c) {
+    int n = c->n();
+    size_t o = 0;
+    c->off_desc = o;
+    o = align_up(o + sizeof(InstDesc) * n);
+    c->off_state = o;
+    o = align_up(o + sizeof(InstState) * n);
+    c->off_order = o;
+    o = align_up(o + sizeof(int) * n);
+    c->off_ident = o;
+    o = align_up(o + sizeof(int) * n);
+    c->off_queue = o;
+    o = align_up(o + sizeof(int) * 64);
+    c->off_tab = o;
+    o = align_up(o + sizeof(Tables<double>) + sizeof(Tables<float>));
+    c->m_off.assign(n, 0);
+    size_t st = 0;
+    for (int i = 0; i < n; ++i) {
+        c->m_off[i] = (long long)st;
+        st += (size_t)nfields_of(c->desc[i].eq) << c->desc[i].Jmax;
+    }
+    c->stage_doubles = st;
+    c->off_stage = o;
+    o = align_up(o + st * sizeof(double));
+    c->inst_off.assign(n, 0);
+    c->hdesc.assign(n, InstDesc{});
+    for (int i = 0; i < n; ++i) {
+        const mr_instance_desc &d = c->desc[i];
+        InstDesc &h = c->hdesc[i];
+        int nf = nfields_of(d.eq), q = 2 * nf;
+        long long S = (1LL << (d.Jmax + 1)) - (1LL << d.Jmin), N = 1LL << d.Jmax;
+        int W = 0;
+        for (int l = d.Jmin; l <= d.Jmax; ++l) W += nwords_h(l);
+        h.Jmin = d.Jmin;
+        h.Jmax = d.Jmax;
+        h.bc = d.bc;
+        h.eq = d.eq;
+        h.nf = nf;
+        h.mu_bar = d.mu_bar;
+        h.Wtot = W;
+        h.eps = d.eps;
+        h.a = d.a;
+        h.b = d.b;
+        h.lam = d.lambda;
+        h.eqp = d.eq_param;
+        for (int j = 0; j < 3; ++j) h.s[j] = d.s[j];
+        h.S = S;
+        h.N = N;
+        h.m_off = c->m_off[i];
+        // FP32 path: details in FP64 on the levels where eps_l falls below
+        // 2^-16 (about 256 single-precision ulps of an O(1) population)
+        h.fp64_detail_upto = -1;
+        if (c->fp32())
+            for (int l = d.Jmin; l <= d.Jmax; ++l)
+                if (std::ldexp(d.eps, l - d.Jmax) < std::ldexp(1.0, -16)) h.fp64_detail_upto = l;
+        c->inst_off[i] = o;
+        size_t vb = c->vbytes();
+        size_t oV = 0, oPhi = align_up(oV + vb * q * S), oM = align_up(oPhi + vb * q * (N + 1));
+        size_t oL = align_up(oM + sizeof(uint32_t) * NMASK * W);
+        // every list holds distinct cells of the instance, so S entries always suffice
+        long long caps[NLIST] = {S, S, S, S, S};
+        long long lo = 0;
+        for (int L = 0; L < NLIST; ++L) {
+            h.list_off[L] = lo;
+            lo += (caps[L] + 63) / 64 * 64;
+        }
+        size_t end = align_up(oL + sizeof(uint32_t) * lo);
+        // pointers are filled at bind time; keep relative offsets for now
+        h.V = (void *)oV;
+        h.Phi = (void *)oPhi;
+        h.masks = (uint32_t *)oM;
+        h.lists = (uint32_t *)oL;
+        o += end;
+    }
+    c->total = align_up(o);
+}
+
+// Reconstruction tables for gamma = 1 (c1 = -1/8), by exact integer recursion.
+// Window recursion one level down (level m -> m+1) on the 4 cells
+// (p-2, p-1, p, p+1) around the first cell p of a leaf, times 8:
+//   rows (2p-2, 2p-1, 2p, 2p+1) = [1 8 -1 0], [-1 8 1 0], [0 1 8 -1], [0 -1 8 1].
+// The first finest cell after dj levels is row 2 of the dj-th power.  At a copy
+// boundary (left edge of cell 0 clamped to itself) the window is (0, 1) and
+// the recursion is [9 -1], [7 1] (times 8).
+static void make_tables(Tables<double> &td, Tables<float> &tf) {
+    typedef __int128 i128;
+    const i128 A[4][4] = {{1, 8, -1, 0}, {-1, 8, 1, 0}, {0, 1, 8, -1}, {0, -1, 8, 1}};
+    const i128 B[2][2] = {{9, -1}, {7, 1}};
+    i128 v[4] = {0, 0, 1, 0}, u[2] = {1, 0};
+    std::memset(&td, 0, sizeof td);
+    std::memset(&tf, 0, sizeof tf);
+    for (int dj = 0; dj <= MAXDJ; ++dj) {
+        for (int j = 0; j < 4; ++j) td.cf[dj][j] = std::ldexp((double)v[j], -3 * dj);
+        for (int j = 0; j < 2; ++j) td.bf[dj][j] = std::ldexp((double)u[j], -3 * dj);
+        if (dj > 0)
+            for (int j = 0; j < 4; ++j) td.t1[dj][j] = td.cf[dj - 1][j];
+        i128 nv[4] = {0, 0, 0, 0}, nu[2] = {0, 0};
+        for (int r = 0; r < 4; ++r)
+            for (int j = 0; j < 4; ++j) nv[j] += v[r] * A[r][j];
+        for (int r = 0; r < 2; ++r)
+            for (int j = 0; j < 2; ++j) nu[j] += u[r] * B[r][j];
+        std::memcpy(v, nv, sizeof v);
+        std::memcpy(u, nu, sizeof u);
+    }
+    for (int dj = 0; dj <= MAXDJ; ++dj) {
+        for (int j = 0; j < 4; ++j) {
+            tf.cf[dj][j] = (float)td.cf[dj][j];
+            tf.t1[dj][j] = (float)td.t1[dj][j];
+        }
+        for (int j = 0; j < 2; ++j) tf.bf[dj][j] = (float)td.bf[dj][j];
+    }
+}
+
+static int launch(mr_ctx *c, int phases, int nsteps, int only_inst, const void *aux0, const void *aux1) {
+    if (!c->bound) return c->fail(MR_ERR_STATE, "context not bound to a workspace");
+    LaunchArgs a{};
+    a.descs = (const InstDesc *)(c->ws + c->off_desc);
+    if (only_inst >= 0) {
+        a.order = (const int *)(c->ws + c->off_ident) + only_inst;
+        a.n = 1;
+    } else {
+        a.order = (const int *)(c->ws + c->off_order);
+        a.n = c->n();
+    }
+    a.nsteps = nsteps;
+    a.phases = phases;
+    a.queue = (int *)(c->ws + c->off_queue);
+    a.aux0 = aux0;
+    a.aux1 = aux1;
+    a.tables = c->ws + c->off_tab + (c->fp32() ? sizeof(Tables<double>) : 0);
+    int rc = c->cuda(cudaMemsetAsync(a.queue, 0, sizeof(int), c->stream), "cudaMemsetAsync");
+    if (rc) return rc;
+    int grid = std::min(a.n, c->grid);
+    int e = mrg_launch(c->fp32(), c->block, std::max(grid, 1), a, c->stream);
+    ++c->launches;
+    if (e) return c->cuda((cudaError_t)e, "kernel launch");
+    return MR_OK;
+}
+
+static int read_state(mr_ctx *c, int inst, InstState *st) {
+    int rc = c->cuda(cudaMemcpyAsync(st, c->ws + c->off_state + sizeof(InstState) * inst, sizeof(InstState),
+                                     cudaMemcpyDeviceToHost, c->stream),
+                     "cudaMemcpyAsync");
+    if (rc) return rc;
+    return c->cuda(cudaStreamSynchronize(c->stream), "cudaStreamSynchronize");
+}
+
+static bool is_device_ptr(const void *p) {
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+// ---------------------------------------------------------------------------
+// C ABI
+
+extern "C" {
+
+mr_status mr_mesh_init(mr_ctx **out, int Jmin, int Jmax, int gamma, double eps, double a, double b, int bc,
+                       int mu_bar, int precision) {
+    if (!out) return MR_ERR_ARG;
+    *out = nullptr;
+    if (precision != MR_FP64 && precision != MR_FP32_MIXED) {
+        g_create_error = "bad precision";
+        return MR_ERR_ARG;
+    }
+    mr_ctx *c = new mr_ctx;
+    c->precision = precision;
+    mr_instance_desc d{};
+    d.Jmin = Jmin;
+    d.Jmax = Jmax;
+    d.gamma = gamma;
+    d.mu_bar = mu_bar;
+    d.bc = bc;
+    d.eq = MR_EQ_ADVECTION;
+    d.eps = eps;
+    d.a = a;
+    d.b = b;
+    d.lambda = 1.0;
+    d.s[0] = d.s[1] = d.s[2] = 1.0;
+    int rc = check_desc(c, d, 0);
+    if (rc) {
+        g_create_error = c->err;
+        delete c;
+        return (mr_status)rc;
+    }
+    c->desc.push_back(d);
+    c->scheme_set.push_back(false);
+    *out = c;
+    return MR_OK;
+}
+
+mr_status lbm_scheme(mr_ctx *c, int d, int q, double lambda, const double *s, int eq, const double *eq_params) {
+    if (!c) return MR_ERR_ARG;
+    if (c->bound) return (mr_status)c->fail(MR_ERR_STATE, "lbm_scheme after mr_bind");
+    if (d != 1) return (mr_status)c->fail(MR_ERR_ARG, "only D = 1 is built");
+    int nf = nfields_of(eq);
+    if (nf == 0 || q != 2 * nf) return (mr_status)c->fail(MR_ERR_ARG, "equilibrium %d needs q = %d (got %d)", eq, 2 * nf, q);
+    if (!s) return (mr_status)c->fail(MR_ERR_ARG, "relaxation rates missing");
+    mr_instance_desc dd = c->desc[0];
+    dd.eq = eq;
+    dd.lambda = lambda;
+    for (int j = 0; j < 3; ++j) dd.s[j] = j < nf ? s[j] : 1.0;
+    dd.eq_param = eq_params ? eq_params[0] : 0.0;
+    if ((eq == MR_EQ_ADVECTION || eq == MR_EQ_SW_VEC || eq == MR_EQ_EULER_VEC) && !eq_params)
+        return (mr_status)c->fail(MR_ERR_ARG, "equilibrium parameter missing");
+    int rc = check_desc(c, dd, 0);
+    if (rc) return (mr_status)rc;
+    c->desc[0] = dd;
+    c->scheme_set[0] = true;
+    return MR_OK;
+}
+
+mr_status mr_batch_create(mr_ctx **out, const mr_instance_desc *desc, int n, int precision) {
+    if (!out) return MR_ERR_ARG;
+    *out = nullptr;
+    if (!desc || n <= 0 || (precision != MR_FP64 && precision != MR_FP32_MIXED)) {
+        g_create_error = "need n > 0 descriptors and a valid precision";
+        return MR_ERR_ARG;
+    }
+    mr_ctx *c = new mr_ctx;
+    c->precision = precision;
+    for (int i = 0; i < n; ++i) {
+        int rc = check_desc(c, desc[i], i);
+        if (rc) {
+            g_create_error = c->err;
+            delete c;
+            return (mr_status)rc;
+        }
+        c->desc.push_back(desc[i]);
+        c->scheme_set.push_back(true);
+    }
+    *out = c;
+    return MR_OK;
+}
+
+mr_status mr_workspace_size(const mr_ctx *cc, size_t *bytes) {
+    mr_ctx *c = const_cast<mr_ctx *>(cc);
+    if (!c || !bytes) return MR_ERR_ARG;
+    for (int i = 0; i < c->n(); ++i)
+        if (!c->scheme_set[i]) return (mr_status)c->fail(MR_ERR_STATE, "scheme of instance %d not set (lbm_scheme)", i);
+    layout(c);
+    *bytes = c->total;
+    return MR_OK;
+}
+
+mr_status mr_bind(mr_ctx *c, void *ws, size_t bytes, void *stream) {
+    if (!c || !ws) return MR_ERR_ARG;
+    size_t need = 0;
+    int rc = mr_workspace_size(c, &need);
+    if (rc) return (mr_status)rc;
+    if (bytes < need) return (mr_status)c->fail(MR_ERR_CAPACITY, "workspace of %zu bytes, need %zu", bytes, need);
+    if (((uintptr_t)ws & 255u) != 0) return (mr_status)c->fail(MR_ERR_ARG, "workspace must be 256-byte aligned");
+    c->ws = (unsigned char *)ws;
+    c->ws_bytes = bytes;
+    c->stream = (cudaStream_t)stream;
+    int dev = 0;
+    if ((rc = c->cuda(cudaGetDevice(&dev), "cudaGetDevice"))) return (mr_status)rc;
+    if ((rc = c->cuda(cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, dev), "attribute"))) return (mr_status)rc;
+    // descriptors with absolute pointers
+    int n = c->n();
+    std::vector<InstDesc> dd = c->hdesc;
+    for (int i = 0; i < n; ++i) {
+        unsigned char *base = c->ws + c->inst_off[i];
+        dd[i].V = base + (size_t)dd[i].V;
+        dd[i].Phi = base + (size_t)dd[i].Phi;
+        dd[i].masks = (uint32_t *)(base + (size_t)dd[i].masks);
+        dd[i].lists = (uint32_t *)(base + (size_t)dd[i].lists);
+        dd[i].st = (InstState *)(c->ws + c->off_state) + i;
+    }
+    c->hdesc = dd;
+    // processing order: largest instances first (q 2^Jmax as the cost estimate)
+    std::vector<int> order(n), ident(n);
+    for (int i = 0; i < n; ++i) order[i] = ident[i] = i;
+    std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
+        double cx = (double)c->hdesc[x].nf * std::ldexp(1.0, c->hdesc[x].Jmax);
+        double cy = (double)c->hdesc[y].nf * std::ldexp(1.0, c->hdesc[y].Jmax);
+        return cx > cy;
+    });
+    Tables<double> td;
+    Tables<float> tf;
+    make_tables(td, tf);
+    cudaStream_t s = c->stream;
+    if ((rc = c->cuda(cudaMemcpyAsync(c->ws + c->off_desc, dd.data(), sizeof(InstDesc) * n, cudaMemcpyHostToDevice, s), "upload")))
+        return (mr_status)rc;
+    if ((rc = c->cuda(cudaMemsetAsync(c->ws + c->off_state, 0, sizeof(InstState) * n, s), "memset"))) return (mr_status)rc;
+    if ((rc = c->cuda(cudaMemcpyAsync(c->ws + c->off_order, order.data(), sizeof(int) * n, cudaMemcpyHostToDevice, s), "upload")))
+        return (mr_status)rc;
+    if ((rc = c->cuda(cudaMemcpyAsync(c->ws + c->off_ident, ident.data(), sizeof(int) * n, cudaMemcpyHostToDevice, s), "upload")))
+        return (mr_status)rc;
+    if ((rc = c->cuda(cudaMemcpyAsync(c->ws + c->off_tab, &td, sizeof td, cudaMemcpyHostToDevice, s), "upload"))) return (mr_status)rc;
+    if ((rc = c->cuda(cudaMemcpyAsync(c->ws + c->off_tab + sizeof td, &tf, sizeof tf, cudaMemcpyHostToDevice, s), "upload")))
+        return (mr_status)rc;
+    if ((rc = c->cuda(cudaStreamSynchronize(s), "cudaStreamSynchronize"))) return (mr_status)rc;
+    // launch shape: one block per instance; 1024 threads for a lone large instance
+    if (c->block == 0) {
+        int jmax = 0;
+        for (auto &d : c->desc) jmax = std::max(jmax, d.Jmax);
+        c->block = n == 1 ? (jmax >= 12 ? 1024 : 512) : 256;
+    }
+    int nb = 0;
+    if ((rc = c->cuda((cudaError_t)mrg_occupancy(c->fp32(), c->block, &nb), "occupancy"))) return (mr_status)rc;
+    c->grid = c->grid_req > 0 ? c->grid_req : std::max(1, nb) * c->sms;
+    c->bound = true;
+    c->initialised = false;
+    return MR_OK;
+}
+
+mr_status mr_set_initial(mr_ctx *c, const double *m, size_t count) {
+    if (!c || !m) return MR_ERR_ARG;
+    if (!c->bound) return (mr_status)c->fail(MR_ERR_STATE, "mr_set_initial before mr_bind");
+    if (count != c->stage_doubles)
+        return (mr_status)c->fail(MR_ERR_CAPACITY, "initial data has %zu values, expected %zu", count, c->stage_doubles);
+    const void *src = m;
+    if (!is_device_ptr(m)) {
+        int rc = c->cuda(cudaMemcpyAsync(c->ws + c->off_stage, m, count * sizeof(double), cudaMemcpyHostToDevice, c->stream),
+                         "cudaMemcpyAsync");
+        if (rc) return (mr_status)rc;
+        src = c->ws + c->off_stage;
+    }
+    int rc = launch(c, PH_INIT_FULL, 0, -1, src, nullptr);
+    if (rc) return (mr_status)rc;
+    c->initialised = true;
+    return MR_OK;
+}
+
+// Host-side check that a complete-tree membership is a sibling-closed graded
+// tree (Def. Tree and Def. Graded tree with gamma = 1) before a kernel reads it.
+static int check_tree(mr_ctx *c, int inst, const unsigned char *Rd) {
+    const mr_instance_desc &d = c->desc[inst];
+    const InstDesc &h = c->hdesc[inst];
+    std::vector<unsigned char> R(h.S);
+    int rc = c->cuda(cudaMemcpy(R.data(), Rd, h.S, cudaMemcpyDeviceToHost), "cudaMemcpy");
+    if (rc) return rc;
+    auto at = [&](int l, long long k) { return R[((1LL << l) - (1LL << d.Jmin)) + k] != 0; };
+    for (long long k = 0; k < (1LL << d.Jmin); ++k)
+        if (!at(d.Jmin, k)) return c->fail(MR_ERR_ARG, "tree: coarsest level must be whole");
+    for (int l = d.Jmin + 1; l <= d.Jmax; ++l) {
+        long long np = 1LL << (l - 1);
+        for (long long k = 0; k < (1LL << l); ++k) {
+            if (!at(l, k)) continue;
+            if (!at(l, k ^ 1)) return c->fail(MR_ERR_ARG, "tree: cell (%d,%lld) without its sibling", l, k);
+            for (int dd = -1; dd <= 1; ++dd) {
+                long long p = (k >> 1) + dd;
+                if (d.bc == MR_BC_PERIODIC)
+                    p = (p + np) % np;
+                else if (p < 0 || p >= np)
+                    continue;
+                if (!at(l - 1, p)) return c->fail(MR_ERR_ARG, "tree: cell (%d,%lld) is not graded", l, k);
+            }
+        }
+    }
+    return MR_OK;
+}
+
+mr_status mr_set_state(mr_ctx *c, int inst, const unsigned char *R, const double *values) {
+    if (!c || !R || !values || inst < 0 || inst >= c->n()) return MR_ERR_ARG;
+    if (!c->bound) return (mr_status)c->fail(MR_ERR_STATE, "mr_set_state before mr_bind");
+    int rc = c->cuda(cudaStreamSynchronize(c->stream), "cudaStreamSynchronize");
+    if (rc) return (mr_status)rc;
+    if ((rc = check_tree(c, inst, R))) return (mr_status)rc;
+    rc = launch(c, PH_INIT_STATE, 0, inst, R, values);
+    if (rc) return (mr_status)rc;
+    c->initialised = true;
+    return MR_OK;
+}
+
+mr_status mr_adapt(mr_ctx *c) {
+    if (!c) return MR_ERR_ARG;
+    if (!c->initialised) return (mr_status)c->fail(MR_ERR_STATE, "no initial state");
+    return (mr_status)launch(c, PH_ADAPT, 1, -1, nullptr, nullptr);
+}
+
+mr_status lbm_step(mr_ctx *c) {
+    if (!c) return MR_ERR_ARG;
+    if (!c->initialised) return (mr_status)c->fail(MR_ERR_STATE, "no initial state");
+    return (mr_status)launch(c, PH_STEP, 1, -1, nullptr, nullptr);
+}
+
+mr_status mr_advance(mr_ctx *c, int nsteps) {
+    if (!c || nsteps < 0) return MR_ERR_ARG;
+    if (!c->initialised) return (mr_status)c->fail(MR_ERR_STATE, "no initial state");
+    if (nsteps == 0) return MR_OK;
+    return (mr_status)launch(c, PH_ADAPT | PH_STEP, nsteps, -1, nullptr, nullptr);
+}
+
+mr_status mr_sync(mr_ctx *c) {
+    if (!c) return MR_ERR_ARG;
+    int rc = c->cuda(cudaStreamSynchronize(c->stream), "cudaStreamSynchronize");
+    if (rc) return (mr_status)rc;
+    if (!c->bound) return MR_OK;
+    std::vector<InstState> st(c->n());
+    rc = c->cuda(cudaMemcpy(st.data(), c->ws + c->off_state, sizeof(InstState) * c->n(), cudaMemcpyDeviceToHost), "cudaMemcpy");
+    if (rc) return (mr_status)rc;
+    for (int i = 0; i < c->n(); ++i)
+        if (st[i].status & ST_NONFINITE) return (mr_status)c->fail(MR_ERR_NONFINITE, "instance %d: non-finite population", i);
+    return MR_OK;
+}
+
+static int fetch_leaves(mr_ctx *c, int inst, std::vector<uint32_t> &ent, std::vector<double> &vals, InstState &st) {
+    int rc = read_state(c, inst, &st);
+    if (rc) return rc;
+    if (st.status & ST_NONFINITE) return c->fail(MR_ERR_NONFINITE, "instance %d: non-finite population", inst);
+    const InstDesc &h = c->hdesc[inst];
+    int q = 2 * h.nf;
+    ent.resize(st.nleaf);
+    if (st.nleaf)
+        if ((rc = c->cuda(cudaMemcpy(ent.data(), h.lists + h.list_off[L_LEAF], sizeof(uint32_t) * st.nleaf, cudaMemcpyDeviceToHost), "copy")))
+            return rc;
+    size_t nv = (size_t)q * h.S;
+    vals.resize(nv);
+    if (c->fp32()) {
+        std::vector<float> tmp(nv);
+        if ((rc = c->cuda(cudaMemcpy(tmp.data(), h.V, sizeof(float) * nv, cudaMemcpyDeviceToHost), "copy"))) return rc;
+        for (size_t i = 0; i < nv; ++i) vals[i] = tmp[i];
+    } else {
+        if ((rc = c->cuda(cudaMemcpy(vals.data(), h.V, sizeof(double) * nv, cudaMemcpyDeviceToHost), "copy"))) return rc;
+    }
+    return MR_OK;
+}
+
+mr_status mr_get_leaves(mr_ctx *c, int inst, int *level, long *index, double *f, long cap, long *count) {
+    if (!c || inst < 0 || inst >= c->n()) return MR_ERR_ARG;
+    if (!c->bound) return (mr_status)c->fail(MR_ERR_STATE, "not bound");
+    std::vector<uint32_t> ent;
+    std::vector<double> vals;
+    InstState st;
+    int rc = fetch_leaves(c, inst, ent, vals, st);
+    if (rc) return (mr_status)rc;
+    if (count) *count = st.nleaf;
+    if ((level || index || f) && cap < st.nleaf) return (mr_status)c->fail(MR_ERR_CAPACITY, "need %d leaf slots", st.nleaf);
+    const InstDesc &h = c->hdesc[inst];
+    int q = 2 * h.nf;
+    for (int i = 0; i < st.nleaf; ++i) {
+        int l = (int)(ent[i] >> KBITS);
+        long k = (long)(ent[i] & KMASK);
+        if (level) level[i] = l;
+        if (index) index[i] = k;
+        if (f) {
+            long long cell = ((1LL << l) - (1LL << h.Jmin)) + k;
+            for (int hh = 0; hh < q; ++hh) f[(long)hh * cap + i] = vals[(size_t)hh * h.S + cell];
+        }
+    }
+    return MR_OK;
+}
+
+mr_status mr_get_moments(mr_ctx *c, int inst, double *m, long cap, long *count) {
+    if (!c || inst < 0 || inst >= c->n()) return MR_ERR_ARG;
+    if (!c->bound) return (mr_status)c->fail(MR_ERR_STATE, "not bound");
+    std::vector<uint32_t> ent;
+    std::vector<double> vals;
+    InstState st;
+    int rc = fetch_leaves(c, inst, ent, vals, st);
+    if (rc) return (mr_status)rc;
+    if (count) *count = st.nleaf;
+    if (m && cap < st.nleaf) return (mr_status)c->fail(MR_ERR_CAPACITY, "need %d leaf slots", st.nleaf);
+    const InstDesc &h = c->hdesc[inst];
+    if (m)
+        for (int i = 0; i < st.nleaf; ++i) {
+            int l = (int)(ent[i] >> KBITS);
+            long long cell = ((1LL << l) - (1LL << h.Jmin)) + (ent[i] & KMASK);
+            for (int j = 0; j < h.nf; ++j)
+                m[(long)j * cap + i] = vals[(size_t)(2 * j) * h.S + cell] + vals[(size_t)(2 * j + 1) * h.S + cell];
+        }
+    return MR_OK;
+}
+
+mr_status mr_get_finest(mr_ctx *c, int inst, double *out) {
+    if (!c || !out || inst < 0 || inst >= c->n()) return MR_ERR_ARG;
+    const InstDesc &h = c->hdesc[inst];
+    bool dev = is_device_ptr(out);
+    void *dst = dev ? (void *)out : (void *)(c->ws + c->off_stage);
+    int rc = launch(c, PH_FINEST, 0, inst, dst, nullptr);
+    if (rc) return (mr_status)rc;
+    if (!dev) {
+        rc = c->cuda(cudaMemcpyAsync(out, dst, sizeof(double) * h.nf * h.N, cudaMemcpyDeviceToHost, c->stream), "copy");
+        if (rc) return (mr_status)rc;
+    }
+    rc = c->cuda(cudaStreamSynchronize(c->stream), "cudaStreamSynchronize");
+    return (mr_status)rc;
+}
+
+mr_status mr_get_tree(mr_ctx *c, int inst, unsigned char *R) {
+    if (!c || !R || inst < 0 || inst >= c->n()) return MR_ERR_ARG;
+    if (!c->bound) return (mr_status)c->fail(MR_ERR_STATE, "not bound");
+    InstState st;
+    int rc = read_state(c, inst, &st);
+    if (rc) return (mr_status)rc;
+    const InstDesc &h = c->hdesc[inst];
+    std::vector<uint32_t> w(h.Wtot);
+    if ((rc = c->cuda(cudaMemcpy(w.data(), h.masks + (size_t)st.cur * h.Wtot, sizeof(uint32_t) * h.Wtot, cudaMemcpyDeviceToHost), "copy")))
+        return (mr_status)rc;
+    int g = 0;
+    for (int l = h.Jmin; l <= h.Jmax; ++l) {
+        long long n = 1LL << l, base = (1LL << l) - (1LL << h.Jmin);
+        for (long long k = 0; k < n; ++k) R[base + k] = (w[g + (k >> 5)] >> (k & 31)) & 1u;
+        g += nwords_h(l);
+    }
+    return MR_OK;
+}
+
+mr_status mr_audit(mr_ctx *c, int inst, double *mass, double *residual) {
+    if (!c || inst < 0 || inst >= c->n()) return MR_ERR_ARG;
+    if (!c->bound) return (mr_status)c->fail(MR_ERR_STATE, "not bound");
+    InstState st;
+    int rc = read_state(c, inst, &st);
+    if (rc) return (mr_status)rc;
+    if (mass)
+        for (int j = 0; j < c->hdesc[inst].nf; ++j) mass[j] = st.mass[j];
+    if (residual) *residual = st.audit;
+    return MR_OK;
+}
+
+mr_status mr_get_summary(mr_ctx *c, double *mass, int *nleaf) {
+    if (!c) return MR_ERR_ARG;
+    if (!c->bound) return (mr_status)c->fail(MR_ERR_STATE, "not bound");
+    const unsigned char *base = c->ws + c->off_state;
+    int rc;
+    if (mass &&
+        (rc = c->cuda(cudaMemcpy2DAsync(mass, 3 * sizeof(double), base + offsetof(InstState, mass), sizeof(InstState),
+                                        3 * sizeof(double), c->n(), cudaMemcpyDeviceToHost, c->stream),
+                      "cudaMemcpy2DAsync")))
+        return (mr_status)rc;
+    if (nleaf &&
+        (rc = c->cuda(cudaMemcpy2DAsync(nleaf, sizeof(int), base + offsetof(InstState, nleaf), sizeof(InstState), sizeof(int),
+                                        c->n(), cudaMemcpyDeviceToHost, c->stream),
+                      "cudaMemcpy2DAsync")))
+        return (mr_status)rc;
+    return (mr_status)c->cuda(cudaStreamSynchronize(c->stream), "cudaStreamSynchronize");
+}
+
+mr_status mr_stats(mr_ctx *c, unsigned long long *updates, unsigned long long *steps, long long *leaves) {
+    if (!c) return MR_ERR_ARG;
+    if (!c->bound) return (mr_status)c->fail(MR_ERR_STATE, "not bound");
+    int rc = c->cuda(cudaStreamSynchronize(c->stream), "cudaStreamSynchronize");
+    if (rc) return (mr_status)rc;
+    std::vector<InstState> st(c->n());
+    rc = c->cuda(cudaMemcpy(st.data(), c->ws + c->off_state, sizeof(InstState) * c->n(), cudaMemcpyDeviceToHost), "copy");
+    if (rc) return (mr_status)rc;
+    unsigned long long u = 0;
+    long long lv = 0;
+    for (auto &s : st) {
+        u += s.updates;
+        lv += s.nleaf;
+    }
+    if (updates) *updates = u;
+    if (steps) *steps = st[0].steps;
+    if (leaves) *leaves = lv;
+    return MR_OK;
+}
+
+mr_status mr_set_launch(mr_ctx *c, int block, int grid) {
+    if (!c) return MR_ERR_ARG;
+    if (block != 128 && block != 256 && block != 512 && block != 1024)
+        return (mr_status)c->fail(MR_ERR_ARG, "block must be 128, 256, 512 or 1024");
+    if (grid < 0) return (mr_status)c->fail(MR_ERR_ARG, "grid must be >= 0");
+    c->block = block;
+    c->grid_req = grid;
+    if (c->bound) {
+        int nb = 0;
+        int rc = c->cuda((cudaError_t)mrg_occupancy(c->fp32(), c->block, &nb), "occupancy");
+        if (rc) return (mr_status)rc;
+        c->grid = grid > 0 ? grid : std::max(1, nb) * c->sms;
+    }
+    return MR_OK;
+}
+
+mr_status mr_reconstruction_coefficients(int dj, int kind, double *out) {
+    if (!out || dj < 0 || dj > MAXDJ || kind < 0 || kind > 2) return MR_ERR_ARG;
+    static Tables<double> td;
+    static Tables<float> tf;
+    static bool made = false;
+    if (!made) {
+        make_tables(td, tf);
+        made = true;
+    }
+    const double *src = kind == 0 ? td.cf[dj] : kind == 1 ? td.t1[dj] : td.bf[dj];
+    int n = kind == 2 ? 2 : 4;
+    for (int j = 0; j < n; ++j) out[j] = src[j];
+    return MR_OK;
+}
+
+mr_status mr_info(const mr_ctx *c, int *n, long long *launches) {
+    if (!c) return MR_ERR_ARG;
+    if (n) *n = (int)c->desc.size();
+    if (launches) *launches = c->launches;
+    return MR_OK;
+}
+
+mr_status mr_last_error(const mr_ctx *c, char *buf, int len) {
+    if (!buf || len <= 0) return MR_ERR_ARG;
+    const std::string &s = c ? c->err : g_create_error;
+    std::snprintf(buf, (size_t)len, "%s", s.c_str());
+    return MR_OK;
+}
+
+mr_status mr_destroy(mr_ctx *c) {
+    delete c;
+    return MR_OK;
+}
+
+}  // extern "C"

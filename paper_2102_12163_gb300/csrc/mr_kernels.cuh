@@ -1,0 +1,885 @@
+// mr_kernels.cuh -- sm_103a kernels of the multiresolution-adaptive lattice
+// Boltzmann step (Bellotti, Gouarin, Graille, Massot, arXiv 2102.12163).
+//
+// One thread block owns one instance at a time and runs every phase of the
+// step on it, separated by block barriers; blocks pull instances from an
+// atomic work queue (persistent launch).  Inside a step:
+//
+//   adapt (Section 4.1)
+//     A1  projection up the current tree (Def. Projection operator)
+//     A2  details of the pairs of the tree, threshold T, Harten flags (Sections
+//         3.2, 3.4, 4.2) -> KEEP / REF bitmasks
+//     A3  enlargement H: same-level dilation and children of REF pairs
+//     A4  grading G, sweeping fine to coarse over bitmask words (Def. Graded
+//         tree), fused with the leaf / transfer / ghost marking
+//     A5  list compaction: popcount + block prefix scan over the mask words
+//     A6  data transfer: prediction of the new cells, coarse to fine
+//   step (Sections 4.3, 4.5)
+//     S1  leaves collision (eq. LeavesCollision)
+//     S2  projection of the collided values up the new tree
+//     S3  ghost prediction coarse to fine (reconstruction operator, Section 3.3)
+//     S4  boundary reconstruction on the first / last finest cell of every
+//         leaf from the per-level-gap tables -> interface array Phi
+//     S5  compact stream (eq. AdaptiveStreamPhase) + FP64 mass audit
+//
+// The cell arrays are dense per level (every cell of every level has a slot),
+// the tree is a set of bitmasks with 32 cells per word, and every per-cell
+// phase walks a compacted list so its work is proportional to the tree.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "mr_common.h"
+
+namespace mrg {
+
+constexpr double C1 = -0.125;  // prediction coefficient c_1 for gamma = 1 (Section 3.1)
+
+// ---------------------------------------------------------------------------
+// arithmetic: the FP64 path uses explicitly rounded operations (never fused)
+// in the collision, so that it follows the same rounding sequence as a plain
+// IEEE evaluation of the formulas; the FP32 path lets the compiler fuse.
+template <typename T>
+struct Ar;
+template <>
+struct Ar<double> {
+    static __device__ __forceinline__ double add(double a, double b) { return __dadd_rn(a, b); }
+    static __device__ __forceinline__ double sub(double a, double b) { return __dsub_rn(a, b); }
+    static __device__ __forceinline__ double mul(double a, double b) { return __dmul_rn(a, b); }
+    static __device__ __forceinline__ double div(double a, double b) { return __ddiv_rn(a, b); }
+};
+template <>
+struct Ar<float> {
+    static __device__ __forceinline__ float add(float a, float b) { return a + b; }
+    static __device__ __forceinline__ float sub(float a, float b) { return a - b; }
+    static __device__ __forceinline__ float mul(float a, float b) { return a * b; }
+    static __device__ __forceinline__ float div(float a, float b) { return a / b; }
+};
+
+template <typename T>
+struct V2;
+template <>
+struct V2<double> {
+    using type = double2;
+};
+template <>
+struct V2<float> {
+    using type = float2;
+};
+
+// ---------------------------------------------------------------------------
+// level geometry and bit helpers
+
+__device__ __forceinline__ long long cell_off(int l, int Jmin) { return (1LL << l) - (1LL << Jmin); }
+__device__ __forceinline__ int nwords(int l) { return l >= 5 ? (1 << (l - 5)) : 1; }
+__device__ __forceinline__ uint32_t valid_bits(int l) {
+    return l >= 5 ? 0xFFFFFFFFu : ((1u << (1 << l)) - 1u);
+}
+// cell index at level l under the boundary condition (0 periodic: wrap, 1 copy: clamp)
+__device__ __forceinline__ long long wrapc(long long k, int l, int bc) {
+    long long n = 1LL << l;
+    if (bc == 0) return k & (n - 1);
+    return k < 0 ? 0 : (k >= n ? n - 1 : k);
+}
+__device__ __forceinline__ uint32_t pack(int l, long long k) { return ((uint32_t)l << KBITS) | (uint32_t)k; }
+
+// bits 0, 2, ..., 30 of x -> bits 0..15
+__device__ __forceinline__ uint32_t compact_even(uint32_t x) {
+    x &= 0x55555555u;
+    x = (x | (x >> 1)) & 0x33333333u;
+    x = (x | (x >> 2)) & 0x0F0F0F0Fu;
+    x = (x | (x >> 4)) & 0x00FF00FFu;
+    x = (x | (x >> 8)) & 0x0000FFFFu;
+    return x;
+}
+// parent bits of two child words (a: cells 0..31, b: cells 32..63)
+__device__ __forceinline__ uint32_t fold2(uint32_t a, uint32_t b) {
+    return compact_even(a | (a >> 1)) | (compact_even(b | (b >> 1)) << 16);
+}
+// 16 parent bits -> 32 child bits (both children of every parent)
+__device__ __forceinline__ uint32_t spread16(uint32_t x) {
+    x &= 0xFFFFu;
+    x = (x | (x << 8)) & 0x00FF00FFu;
+    x = (x | (x << 4)) & 0x0F0F0F0Fu;
+    x = (x | (x << 2)) & 0x33333333u;
+    x = (x | (x << 1)) & 0x55555555u;
+    return x | (x << 1);
+}
+// close a set of cells under siblings (pairs 2p, 2p+1 never straddle a word)
+__device__ __forceinline__ uint32_t pairexpand(uint32_t x) {
+    return x | ((x & 0x55555555u) << 1) | ((x & 0xAAAAAAAAu) >> 1);
+}
+// word wp of level l-1 holding the parents of the cells set in level l (words `child`)
+__device__ __forceinline__ uint32_t fold_at(const uint32_t *child, int l, int wp) {
+    return l >= 6 ? fold2(child[2 * wp], child[2 * wp + 1]) : fold2(child[0], 0u);
+}
+
+// Dilation by r cells of the set held in word wi of level l; get(j) returns word j
+// of that level.  Periodic: wrap; copy: cells beyond the domain are dropped.
+template <class Get>
+__device__ __forceinline__ uint32_t dilate(Get get, int l, int wi, int r, int bc) {
+    uint32_t x = get(wi);
+    uint32_t out = x;
+    if (l < 5) {
+        int n = 1 << l;
+        uint32_t vb = (1u << n) - 1u;
+        for (int s = 1; s <= r; ++s) {
+            if (bc == 0)
+                out |= (((x << s) | (x >> (n - s))) & vb) | (((x >> s) | (x << (n - s))) & vb);
+            else
+                out |= ((x << s) & vb) | (x >> s);
+        }
+        return out;
+    }
+    int W = 1 << (l - 5);
+    uint32_t xl, xr;
+    if (W == 1) {
+        xl = xr = (bc == 0) ? x : 0u;
+    } else if (bc == 0) {
+        xl = get((wi - 1) & (W - 1));
+        xr = get((wi + 1) & (W - 1));
+    } else {
+        xl = wi > 0 ? get(wi - 1) : 0u;
+        xr = wi + 1 < W ? get(wi + 1) : 0u;
+    }
+    for (int s = 1; s <= r; ++s) out |= (x << s) | (xl >> (32 - s)) | (x >> s) | (xr << (32 - s));
+    return out;
+}
+
+// ---------------------------------------------------------------------------
+// shared memory
+
+template <typename T>
+struct Smem {
+    Tables<T> tab;
+    InstDesc d;
+    int woff[MAXLEV + 2];
+    int seg[NLIST][MAXLEV + 2];
+    int scan_w[NLIST][32];
+    int scan_tot[NLIST];
+    double red[3][32];
+    double mass[3];
+    double audit;
+    unsigned long long updates, steps;
+    int cur, nleaf, status, near_ties;
+    int idx;
+    int g0s, gbase;  // level_of_word constants
+};
+
+template <typename T>
+__device__ __forceinline__ void level_of_word(const Smem<T> &sm, int g, int &l, int &wi) {
+    if (g < sm.g0s) {
+        l = sm.d.Jmin + g;
+        wi = 0;
+    } else {
+        int x = g - sm.g0s + sm.gbase;
+        l = 5 + (31 - __clz(x));
+        wi = x - (1 << (l - 5));
+    }
+}
+
+// ---------------------------------------------------------------------------
+// scheme: vectorial D1Q2^n (Section 2.1, equilibria of Sections 5.1 and 5.3)
+
+template <typename T, int NF>
+__device__ __forceinline__ void equilibria(int eq, T eqp, const T *mc, T *meq) {
+    using A = Ar<T>;
+    if constexpr (NF == 1) {
+        if (eq == 0)
+            meq[0] = A::mul(eqp, mc[0]);  // advection: c m0
+        else
+            meq[0] = A::mul(T(0.5), A::mul(mc[0], mc[0]));  // Burgers: m0^2 / 2
+    } else if constexpr (NF == 2) {
+        // shallow water (h, hu): hu, hu^2 / h + g h^2 / 2
+        meq[0] = mc[1];
+        meq[1] = A::add(A::div(A::mul(mc[1], mc[1]), mc[0]), A::mul(A::mul(T(0.5), eqp), A::mul(mc[0], mc[0])));
+    } else {
+        // Euler (rho, rho u, E), Section 5.3
+        T gg = eqp;
+        T u2 = A::mul(mc[1], mc[1]);
+        meq[0] = mc[1];
+        meq[1] = A::add(A::mul(A::sub(T(1.5), A::mul(T(0.5), gg)), A::div(u2, mc[0])), A::mul(A::sub(gg, T(1)), mc[2]));
+        meq[2] = A::add(A::mul(gg, A::div(A::mul(mc[2], mc[1]), mc[0])),
+                        A::mul(A::mul(T(0.5), A::sub(T(1), gg)), A::div(A::mul(u2, mc[1]), A::mul(mc[0], mc[0]))));
+    }
+}
+
+// leaves collision on the q populations of one cell: m = M f, relax, f* = M^-1 m*
+template <typename T, int NF>
+__device__ __forceinline__ void collide(const InstDesc &d, T *f) {
+    using A = Ar<T>;
+    T mc[NF], mn[NF], meq[NF];
+    const T lam = (T)d.lam;
+#pragma unroll
+    for (int i = 0; i < NF; ++i) {
+        mc[i] = A::add(f[2 * i], f[2 * i + 1]);
+        mn[i] = A::mul(lam, A::sub(f[2 * i], f[2 * i + 1]));
+    }
+    equilibria<T, NF>(d.eq, (T)d.eqp, mc, meq);
+#pragma unroll
+    for (int i = 0; i < NF; ++i) {
+        T s = (T)d.s[i];
+        T mstar = A::add(A::mul(A::sub(T(1), s), mn[i]), A::mul(s, meq[i]));
+        T g = A::div(mstar, lam);
+        f[2 * i] = A::mul(T(0.5), A::add(mc[i], g));
+        f[2 * i + 1] = A::mul(T(0.5), A::sub(mc[i], g));
+    }
+}
+
+// populations at equilibrium of the conserved moments (initial datum), in FP64
+template <int NF>
+__device__ __forceinline__ void equilibrium_populations(const InstDesc &d, const double *mc, double *f) {
+    using A = Ar<double>;
+    double meq[NF];
+    equilibria<double, NF>(d.eq, d.eqp, mc, meq);
+#pragma unroll
+    for (int i = 0; i < NF; ++i) {
+        double g = A::div(meq[i], d.lam);
+        f[2 * i] = A::mul(0.5, A::add(mc[i], g));
+        f[2 * i + 1] = A::mul(0.5, A::sub(mc[i], g));
+    }
+}
+
+// prediction of child `odd` of cell p of a row at level lp (Section 3.1, gamma = 1)
+template <typename T>
+__device__ __forceinline__ T predict(const T *row, long long p, int odd, int lp, int bc) {
+    T vl = row[wrapc(p - 1, lp, bc)], vp = row[p], vr = row[wrapc(p + 1, lp, bc)];
+    T t = T(C1) * (vr - vl);  // exact: c_1 is a power of two
+    return odd ? vp - t : vp + t;
+}
+
+// ---------------------------------------------------------------------------
+// the instance worker
+
+template <typename T, int NF, int NT>
+struct Worker {
+    static constexpr int Q = 2 * NF;
+    Smem<T> &sm;
+    const InstDesc &d;
+    T *V;
+    T *Phi;
+    uint32_t *M;  // mask base
+    int tid;
+
+    __device__ Worker(Smem<T> &s) : sm(s), d(s.d), tid(threadIdx.x) {
+        V = (T *)d.V;
+        Phi = (T *)d.Phi;
+        M = d.masks;
+    }
+
+    __device__ __forceinline__ uint32_t *mask(int m) { return M + (long long)m * d.Wtot; }
+    __device__ __forceinline__ uint32_t *list(int L) { return d.lists + d.list_off[L]; }
+    __device__ __forceinline__ T *row(int h, int l) { return V + (long long)h * d.S + cell_off(l, d.Jmin); }
+
+    // ---- A1 / S2: projection up the tree over the internal cells ----------
+    __device__ void upsweep() {
+        const uint32_t *lst = list(L_INT);
+        for (int l = d.Jmax - 1; l >= d.Jmin; --l) {
+            int b = sm.seg[L_INT][l], e = sm.seg[L_INT][l + 1];
+            if (b == e) continue;
+            for (int i = b + tid; i < e; i += NT) {
+                long long k = lst[i] & KMASK;
+#pragma unroll
+                for (int h = 0; h < Q; ++h) {
+                    typename V2<T>::type c = *reinterpret_cast<const typename V2<T>::type *>(row(h, l + 1) + 2 * k);
+                    row(h, l)[k] = T(0.5) * (c.x + c.y);
+                }
+            }
+            __syncthreads();
+        }
+    }
+
+    // ---- A2: details, threshold T, Harten flags ----------------------------
+    __device__ void details() {
+        const uint32_t *lst = list(L_EVEN);
+        int b = sm.seg[L_EVEN][d.Jmin + 1], e = sm.seg[L_EVEN][d.Jmax + 1];
+        uint32_t *keep = mask(M_KEEP), *ref = mask(M_REF);
+        for (int i = b + tid; i < e; i += NT) {
+            uint32_t ent = lst[i];
+            int l = ent >> KBITS;
+            long long k = ent & KMASK, p = k >> 1;
+            double D = 0.0;
+            bool wide = sizeof(T) == 8 || l <= d.fp64_detail_upto;
+#pragma unroll
+            for (int h = 0; h < Q; ++h) {
+                const T *rc = row(h, l - 1);
+                double dv;
+                if (wide) {
+                    double vl = (double)rc[wrapc(p - 1, l - 1, d.bc)], vp = (double)rc[p],
+                           vr = (double)rc[wrapc(p + 1, l - 1, d.bc)];
+                    dv = (double)row(h, l)[k] - (vp + C1 * (vr - vl));
+                } else {
+                    dv = (double)(row(h, l)[k] - predict<T>(rc, p, 0, l - 1, d.bc));
+                }
+                D = fmax(D, fabs(dv));
+            }
+            double eps_l = ldexp(d.eps, l - d.Jmax);
+            double big = ldexp(eps_l, d.mu_bar + 1);
+            int w = (int)(k >> 5);
+            uint32_t bits = 3u << (k & 31);
+            if (fabs(D - eps_l) <= 1e-12 * eps_l || (l < d.Jmax && fabs(D - big) <= 1e-12 * big))
+                atomicAdd(&sm.near_ties, 1);
+            if (D >= eps_l) {
+                atomicOr(&keep[sm.woff[l] + w], bits);
+                if (l < d.Jmax && D >= big) atomicOr(&ref[sm.woff[l] + w], bits);
+            }
+        }
+    }
+
+    // ---- A3: R(H(T)) per word ------------------------------------------------
+    __device__ void enlarge(uint32_t *Rn) {
+        const uint32_t *keep = mask(M_KEEP), *ref = mask(M_REF);
+        for (int g = tid; g < d.Wtot; g += NT) {
+            int l, wi;
+            level_of_word(sm, g, l, wi);
+            uint32_t vb = valid_bits(l), rh;
+            if (l == d.Jmin) {
+                rh = vb;
+            } else {
+                const uint32_t *kl = keep + sm.woff[l];
+                uint32_t rt = kl[wi];
+                rh = rt | pairexpand(dilate([&](int j) { return kl[j]; }, l, wi, 1, d.bc));
+                if (l >= d.Jmin + 2) rh |= spread16(ref[sm.woff[l - 1] + (wi >> 1)] >> (16 * (wi & 1)));
+            }
+            Rn[g] = rh & vb;
+        }
+    }
+
+    // ---- A4: grading sweep + leaf / transfer / ghost marking -----------------
+    // grade = false only re-derives the marks of a tree known to be graded.
+    __device__ void grade_and_mark(uint32_t *Rn, const uint32_t *Ro, bool grade) {
+        uint32_t *LF = mask(M_LEAF), *PR = mask(M_PRED), *GH = mask(M_GH);
+        for (int l = d.Jmax; l >= d.Jmin; --l) {
+            const uint32_t *rl = Rn + sm.woff[l];
+            const uint32_t *rf = l < d.Jmax ? Rn + sm.woff[l + 1] : nullptr;
+            if (grade && l > d.Jmin + 1) {
+                // (l-1, floor(k/2) + delta), |delta| <= gamma, with siblings
+                uint32_t *rp = Rn + sm.woff[l - 1];
+                int Wp = nwords(l - 1);
+                uint32_t vb = valid_bits(l - 1);
+                for (int wp = tid; wp < Wp; wp += NT)
+                    rp[wp] |= pairexpand(dilate([&](int j) { return fold_at(rl, l, j); }, l - 1, wp, 1, d.bc)) & vb;
+            }
+            int W = nwords(l);
+            uint32_t vb = valid_bits(l);
+            const uint32_t *pf = l < d.Jmax ? PR + sm.woff[l + 1] : nullptr;
+            const uint32_t *gf = l < d.Jmax ? GH + sm.woff[l + 1] : nullptr;
+            auto leafw = [&](int j) { return rf ? (rl[j] & ~fold_at(rf, l + 1, j)) : rl[j]; };
+            for (int wi = tid; wi < W; wi += NT) {
+                uint32_t lf = leafw(wi);
+                uint32_t ro = Ro[sm.woff[l] + wi];
+                uint32_t pr = lf & ~ro, gh = 0;
+                if (rf) {
+                    pr |= dilate([&](int j) { return fold_at(pf, l + 1, j); }, l, wi, 1, d.bc) & ~ro;
+                    gh = dilate(leafw, l, wi, 2, d.bc) | dilate([&](int j) { return fold_at(gf, l + 1, j); }, l, wi, 1, d.bc);
+                }
+                LF[sm.woff[l] + wi] = lf & vb;
+                PR[sm.woff[l] + wi] = pr & vb;
+                GH[sm.woff[l] + wi] = gh & ~rl[wi] & vb;
+            }
+            __syncthreads();
+        }
+    }
+
+    // ---- A5: list compaction -------------------------------------------------
+    __device__ void block_scan(int (&v)[NLIST], int (&excl)[NLIST]) {
+        int lane = tid & 31, warp = tid >> 5;
+        int inc[NLIST];
+#pragma unroll
+        for (int L = 0; L < NLIST; ++L) {
+            int x = v[L];
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                int y = __shfl_up_sync(0xFFFFFFFFu, x, o);
+                if (lane >= o) x += y;
+            }
+            inc[L] = x;
+            if (lane == 31) sm.scan_w[L][warp] = x;
+        }
+        __syncthreads();
+        if (warp == 0) {
+#pragma unroll
+            for (int L = 0; L < NLIST; ++L) {
+                int x0 = lane < NT / 32 ? sm.scan_w[L][lane] : 0, x = x0;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    int y = __shfl_up_sync(0xFFFFFFFFu, x, o);
+                    if (lane >= o) x += y;
+                }
+                sm.scan_w[L][lane] = x - x0;
+                if (lane == 31) sm.scan_tot[L] = x;
+            }
+        }
+        __syncthreads();
+#pragma unroll
+        for (int L = 0; L < NLIST; ++L) excl[L] = sm.scan_w[L][warp] + inc[L] - v[L];
+    }
+
+    __device__ __forceinline__ void word_lists(const uint32_t *Rn, int g, int l, uint32_t (&m)[NLIST]) {
+        uint32_t r = Rn[g], lf = mask(M_LEAF)[g];
+        m[L_INT] = r & ~lf;
+        m[L_EVEN] = l > d.Jmin ? (r & 0x55555555u) : 0u;
+        m[L_LEAF] = lf;
+        m[L_PRED] = mask(M_PRED)[g];
+        m[L_GH] = mask(M_GH)[g];
+    }
+
+    __device__ void build_lists(const uint32_t *Rn) {
+        int C = (d.Wtot + NT - 1) / NT;
+        int g0 = tid * C, g1 = min(d.Wtot, g0 + C);
+        int cnt[NLIST] = {0, 0, 0, 0, 0}, off[NLIST];
+        for (int g = g0; g < g1; ++g) {
+            int l, wi;
+            level_of_word(sm, g, l, wi);
+            uint32_t m[NLIST];
+            word_lists(Rn, g, l, m);
+#pragma unroll
+            for (int L = 0; L < NLIST; ++L) cnt[L] += __popc(m[L]);
+        }
+        block_scan(cnt, off);
+        for (int g = g0; g < g1; ++g) {
+            int l, wi;
+            level_of_word(sm, g, l, wi);
+            if (wi == 0)
+#pragma unroll
+                for (int L = 0; L < NLIST; ++L) sm.seg[L][l] = off[L];
+            uint32_t m[NLIST];
+            word_lists(Rn, g, l, m);
+#pragma unroll
+            for (int L = 0; L < NLIST; ++L) {
+                uint32_t *dst = list(L);
+                uint32_t x = m[L];
+                while (x) {
+                    int bit = __ffs(x) - 1;
+                    x &= x - 1;
+                    dst[off[L]++] = pack(l, 32LL * wi + bit);
+                }
+            }
+        }
+        if (tid == 0) {
+#pragma unroll
+            for (int L = 0; L < NLIST; ++L) sm.seg[L][d.Jmax + 1] = sm.scan_tot[L];
+            sm.nleaf = sm.scan_tot[L_LEAF];
+        }
+        __syncthreads();
+    }
+
+    // ---- A6 / S3: prediction of listed cells, coarse to fine -----------------
+    __device__ void predict_fill(int L) {
+        const uint32_t *lst = list(L);
+        for (int l = d.Jmin + 1; l <= d.Jmax; ++l) {
+            int b = sm.seg[L][l], e = sm.seg[L][l + 1];
+            if (b == e) continue;
+            for (int i = b + tid; i < e; i += NT) {
+                long long k = lst[i] & KMASK;
+#pragma unroll
+                for (int h = 0; h < Q; ++h) row(h, l)[k] = predict<T>(row(h, l - 1), k >> 1, (int)(k & 1), l - 1, d.bc);
+            }
+            __syncthreads();
+        }
+    }
+
+    // ---- mesh adaptation ----------------------------------------------------
+    __device__ void adapt() {
+        uint32_t *Ro = mask(sm.cur), *Rn = mask(sm.cur ^ 1);
+        uint32_t *keep = mask(M_KEEP), *ref = mask(M_REF);
+        for (int g = tid; g < d.Wtot; g += NT) {
+            keep[g] = 0u;
+            ref[g] = 0u;
+        }
+        upsweep();  // ends with a barrier unless no level has internal cells
+        __syncthreads();
+        details();
+        __syncthreads();
+        enlarge(Rn);
+        __syncthreads();
+        grade_and_mark(Rn, Ro, true);
+        build_lists(Rn);
+        predict_fill(L_PRED);
+        if (tid == 0) {
+            sm.cur ^= 1;
+            sm.updates += (unsigned long long)sm.nleaf;
+        }
+        __syncthreads();
+    }
+
+    // ---- one step of the adaptive scheme on the current mesh -----------------
+    __device__ void lbm_step() {
+        const uint32_t *leaves = list(L_LEAF);
+        int nl = sm.nleaf;
+        // S1 leaves collision
+        for (int i = tid; i < nl; i += NT) {
+            uint32_t ent = leaves[i];
+            int l = ent >> KBITS;
+            long long k = ent & KMASK;
+            T f[Q];
+#pragma unroll
+            for (int h = 0; h < Q; ++h) f[h] = row(h, l)[k];
+            collide<T, NF>(d, f);
+#pragma unroll
+            for (int h = 0; h < Q; ++h) row(h, l)[k] = f[h];
+        }
+        __syncthreads();
+        upsweep();             // S2
+        predict_fill(L_GH);    // S3
+        reconstruct_edges();   // S4
+        __syncthreads();
+        stream_and_audit();    // S5
+    }
+
+    // S4: first / last finest-cell values of every leaf -> Phi
+    __device__ void reconstruct_edges() {
+        const uint32_t *leaves = list(L_LEAF);
+        const uint32_t *R = mask(sm.cur);
+        const long long N = d.N;
+        const int bc = d.bc;
+        for (int i = tid; i < sm.nleaf; i += NT) {
+            uint32_t ent = leaves[i];
+            int l = ent >> KBITS;
+            long long k = ent & KMASK;
+            int dj = d.Jmax - l;
+            long long nl = 1LL << l;
+            bool at_left = bc == 1 && k == 0, at_right = bc == 1 && k == nl - 1;
+            bool fin_l = false, fin_r = false;
+            if (dj > 0) {
+                const uint32_t *rf = R + sm.woff[l + 1];
+                if (!at_left) {
+                    long long c = 2 * wrapc(k - 1, l, bc);
+                    fin_l = (rf[c >> 5] >> (c & 31)) & 1u;
+                }
+                if (!at_right) {
+                    long long c = 2 * wrapc(k + 1, l, bc);
+                    fin_r = (rf[c >> 5] >> (c & 31)) & 1u;
+                }
+            }
+            const T *cf = sm.tab.cf[dj], *t1 = sm.tab.t1[dj], *bf = sm.tab.bf[dj];
+#pragma unroll
+            for (int h = 0; h < Q; ++h) {
+                const T *r = row(h, l);
+                const bool plus = (h & 1) == 0;  // velocity +lambda
+                bool need_first = !plus || at_left, need_last = plus || at_right;
+                T rfirst = T(0), rlast = T(0);
+                if (dj == 0) {
+                    rfirst = rlast = r[k];
+                } else {
+                    T vm1 = r[wrapc(k - 1, l, bc)], v0 = r[k], vp1 = r[wrapc(k + 1, l, bc)];
+                    T tt = T(C1) * (vp1 - vm1);
+                    T pe = v0 + tt, po = v0 - tt;  // children of the leaf
+                    const T *rf = row(h, l + 1);
+                    if (need_first) {
+                        if (at_left) {
+                            rfirst = bf[0] * v0 + bf[1] * vp1;
+                        } else if (fin_l) {
+                            long long c = 2 * wrapc(k - 1, l, bc);
+                            rfirst = dot4(t1[0], rf[c], t1[1], rf[c + 1], t1[2], pe, t1[3], po);
+                        } else {
+                            rfirst = dot4(cf[0], r[wrapc(k - 2, l, bc)], cf[1], vm1, cf[2], v0, cf[3], vp1);
+                        }
+                    }
+                    if (need_last) {
+                        if (at_right) {
+                            rlast = bf[0] * v0 + bf[1] * vm1;
+                        } else if (fin_r) {
+                            long long c = 2 * wrapc(k + 1, l, bc);
+                            rlast = dot4(t1[3], pe, t1[2], po, t1[1], rf[c], t1[0], rf[c + 1]);
+                        } else {
+                            rlast = dot4(cf[3], vm1, cf[2], v0, cf[1], vp1, cf[0], r[wrapc(k + 2, l, bc)]);
+                        }
+                    }
+                }
+                T *ph = Phi + (long long)h * (N + 1);
+                if (plus) {
+                    long long ix = (k + 1) << dj;
+                    if (bc == 0) ix &= N - 1;
+                    ph[ix] = rlast;
+                    if (at_left) ph[0] = rfirst;
+                } else {
+                    ph[k << dj] = rfirst;
+                    if (at_right) ph[N] = rlast;
+                }
+            }
+        }
+    }
+
+    // sum of four products; FP32: compensated (Kahan) accumulation
+    static __device__ __forceinline__ T dot4(T c0, T x0, T c1, T x1, T c2, T x2, T c3, T x3) {
+        if constexpr (sizeof(T) == 8) {
+            return fma(c3, x3, fma(c2, x2, fma(c1, x1, c0 * x0)));
+        } else {
+            T p[4] = {c0 * x0, c1 * x1, c2 * x2, c3 * x3};
+            T s = T(0), comp = T(0);
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                T y = p[j] - comp;
+                T t = s + y;
+                comp = (t - s) - y;
+                s = t;
+            }
+            return s;
+        }
+    }
+
+    // S5: f^{n+1} = f* + sigma 2^-dj (Phi[first] - Phi[next]); FP64 mass audit
+    __device__ void stream_and_audit() {
+        const uint32_t *leaves = list(L_LEAF);
+        const long long N = d.N;
+        double macc[NF];
+#pragma unroll
+        for (int j = 0; j < NF; ++j) macc[j] = 0.0;
+        bool bad = false;
+        for (int i = tid; i < sm.nleaf; i += NT) {
+            uint32_t ent = leaves[i];
+            int l = ent >> KBITS;
+            long long k = ent & KMASK;
+            int dj = d.Jmax - l;
+            long long first = k << dj, next = (k + 1) << dj;
+            if (d.bc == 0) next &= N - 1;
+            double dx = ldexp(d.b - d.a, -l);
+            T fn[Q];
+#pragma unroll
+            for (int h = 0; h < Q; ++h) {
+                const T *ph = Phi + (long long)h * (N + 1);
+                T coef = (h & 1) ? -ldexpf(1.0f, -dj) : ldexpf(1.0f, -dj);
+                T *r = row(h, l);
+                T v = r[k] + coef * (ph[first] - ph[next]);
+                bad |= !isfinite(v);
+                r[k] = v;
+                fn[h] = v;
+            }
+#pragma unroll
+            for (int j = 0; j < NF; ++j) macc[j] += dx * ((double)fn[2 * j] + (double)fn[2 * j + 1]);
+        }
+        // block reduction of the FP64 totals
+        int lane = tid & 31, warp = tid >> 5;
+#pragma unroll
+        for (int j = 0; j < NF; ++j) {
+            double x = macc[j];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xFFFFFFFFu, x, o);
+            if (lane == 0) sm.red[j][warp] = x;
+        }
+        if (bad) atomicOr(&sm.status, (int)ST_NONFINITE);
+        __syncthreads();
+        if (tid == 0) {
+            double dxJ = ldexp(d.b - d.a, -d.Jmax);
+            for (int j = 0; j < NF; ++j) {
+                double tot = 0.0;
+                for (int w = 0; w < NT / 32; ++w) tot += sm.red[j][w];
+                double flux = 0.0;
+                if (d.bc == 1) {
+                    const T *pp = Phi + (long long)(2 * j) * (N + 1), *pm = Phi + (long long)(2 * j + 1) * (N + 1);
+                    flux = dxJ * (((double)pp[0] - (double)pp[N]) - ((double)pm[0] - (double)pm[N]));
+                }
+                double res = fabs(tot - sm.mass[j] - flux);
+                sm.audit = fmax(sm.audit, res);
+                sm.mass[j] = tot;
+            }
+            sm.steps += 1ULL;
+        }
+        __syncthreads();
+    }
+
+    // ---- initial state -------------------------------------------------------
+    // full tree, populations at equilibrium of the conserved moments (staged m_cons)
+    __device__ void init_full(const double *mcons) {
+        uint32_t *R = mask(M_R0);
+        for (int g = tid; g < d.Wtot; g += NT) {
+            int l, wi;
+            level_of_word(sm, g, l, wi);
+            R[g] = valid_bits(l);
+        }
+        const long long N = d.N;
+        for (long long k = tid; k < N; k += NT) {
+            double mc[NF], f[Q];
+#pragma unroll
+            for (int j = 0; j < NF; ++j) mc[j] = mcons[j * N + k];
+            equilibrium_populations<NF>(d, mc, f);
+#pragma unroll
+            for (int h = 0; h < Q; ++h) row(h, d.Jmax)[k] = (T)f[h];
+        }
+        if (tid == 0) sm.cur = M_R0;
+        __syncthreads();
+        finish_init();
+    }
+
+    // arbitrary graded tree (one byte per cell) and values
+    __device__ void init_state(const unsigned char *Rb, const double *vals) {
+        uint32_t *R = mask(M_R0);
+        for (int g = tid; g < d.Wtot; g += NT) {
+            int l, wi;
+            level_of_word(sm, g, l, wi);
+            long long base = cell_off(l, d.Jmin) + 32LL * wi;
+            int nb = l >= 5 ? 32 : (1 << l);
+            uint32_t w = 0;
+            for (int b = 0; b < nb; ++b) w |= (Rb[base + b] ? 1u : 0u) << b;
+            R[g] = w;
+        }
+        for (long long c = tid; c < (long long)Q * d.S; c += NT) V[c] = (T)vals[c];
+        if (tid == 0) sm.cur = M_R0;
+        __syncthreads();
+        finish_init();
+    }
+
+    __device__ void finish_init() {
+        uint32_t *R = mask(sm.cur);
+        grade_and_mark(R, R, false);  // PRED empty: the tree is its own old tree
+        build_lists(R);
+        // FP64 totals of the initial leaves
+        const uint32_t *leaves = list(L_LEAF);
+        double macc[NF];
+#pragma unroll
+        for (int j = 0; j < NF; ++j) macc[j] = 0.0;
+        for (int i = tid; i < sm.nleaf; i += NT) {
+            uint32_t ent = leaves[i];
+            int l = ent >> KBITS;
+            long long k = ent & KMASK;
+            double dx = ldexp(d.b - d.a, -l);
+#pragma unroll
+            for (int j = 0; j < NF; ++j) macc[j] += dx * ((double)row(2 * j, l)[k] + (double)row(2 * j + 1, l)[k]);
+        }
+        int lane = tid & 31, warp = tid >> 5;
+#pragma unroll
+        for (int j = 0; j < NF; ++j) {
+            double x = macc[j];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xFFFFFFFFu, x, o);
+            if (lane == 0) sm.red[j][warp] = x;
+        }
+        __syncthreads();
+        if (tid == 0) {
+            for (int j = 0; j < NF; ++j) {
+                double tot = 0.0;
+                for (int w = 0; w < NT / 32; ++w) tot += sm.red[j][w];
+                sm.mass[j] = tot;
+            }
+            sm.audit = 0.0;
+            sm.status = 0;
+            sm.near_ties = 0;
+            sm.updates = 0ULL;
+            sm.steps = 0ULL;
+        }
+        __syncthreads();
+    }
+
+    // ---- multiresolution reconstruction on the finest level (measurement) ----
+    __device__ void finest(double *out) {
+        upsweep();
+        __syncthreads();
+        const uint32_t *R = mask(sm.cur);
+        for (int l = d.Jmin + 1; l <= d.Jmax; ++l) {
+            long long n = 1LL << l;
+            const uint32_t *rl = R + sm.woff[l];
+            for (long long k = tid; k < n; k += NT)
+                if (!((rl[k >> 5] >> (k & 31)) & 1u))
+#pragma unroll
+                    for (int h = 0; h < Q; ++h) row(h, l)[k] = predict<T>(row(h, l - 1), k >> 1, (int)(k & 1), l - 1, d.bc);
+            __syncthreads();
+        }
+        const long long N = d.N;
+        for (long long k = tid; k < N; k += NT)
+#pragma unroll
+            for (int j = 0; j < NF; ++j) out[j * N + k] = (double)row(2 * j, d.Jmax)[k] + (double)row(2 * j + 1, d.Jmax)[k];
+        __syncthreads();
+    }
+};
+
+// ---------------------------------------------------------------------------
+
+template <typename T>
+__device__ void load_instance(Smem<T> &sm, const InstDesc &dg) {
+    int tid = threadIdx.x;
+    if (tid == 0) {
+        sm.d = dg;
+        const InstState &st = *dg.st;
+        sm.cur = st.cur;
+        sm.nleaf = st.nleaf;
+        sm.status = st.status;
+        sm.near_ties = st.near_ties;
+        sm.updates = st.updates;
+        sm.steps = st.steps;
+        sm.audit = st.audit;
+        for (int j = 0; j < 3; ++j) sm.mass[j] = st.mass[j];
+        int Jmin = dg.Jmin, Jmax = dg.Jmax;
+        int o = 0;
+        for (int l = Jmin; l <= Jmax; ++l) {
+            sm.woff[l] = o;
+            o += l >= 5 ? (1 << (l - 5)) : 1;
+        }
+        sm.woff[Jmax + 1] = o;
+        sm.g0s = Jmin < 5 ? 5 - Jmin : 0;
+        sm.gbase = Jmin < 5 ? 1 : (1 << (Jmin - 5));
+    }
+    for (int i = tid; i < NLIST * (MAXLEV + 2); i += blockDim.x) (&sm.seg[0][0])[i] = (&dg.st->seg[0][0])[i];
+    __syncthreads();
+}
+
+template <typename T>
+__device__ void store_instance(Smem<T> &sm) {
+    int tid = threadIdx.x;
+    InstState &st = *sm.d.st;
+    if (tid == 0) {
+        st.cur = sm.cur;
+        st.nleaf = sm.nleaf;
+        st.status = sm.status;
+        st.near_ties = sm.near_ties;
+        st.updates = sm.updates;
+        st.steps = sm.steps;
+        st.audit = sm.audit;
+        for (int j = 0; j < 3; ++j) st.mass[j] = sm.mass[j];
+    }
+    for (int i = tid; i < NLIST * (MAXLEV + 2); i += blockDim.x) (&st.seg[0][0])[i] = (&sm.seg[0][0])[i];
+    __syncthreads();
+}
+
+template <typename T, int NF, int NT>
+__device__ void run_instance(Smem<T> &sm, const LaunchArgs &a) {
+    Worker<T, NF, NT> w(sm);
+    if (a.phases & PH_INIT_FULL) w.init_full((const double *)a.aux0 + sm.d.m_off);
+    if (a.phases & PH_INIT_STATE) w.init_state((const unsigned char *)a.aux0, (const double *)a.aux1);
+    for (int n = 0; n < a.nsteps; ++n) {
+        if (a.phases & PH_ADAPT) w.adapt();
+        if (a.phases & PH_STEP) w.lbm_step();
+    }
+    if (a.phases & PH_FINEST) w.finest((double *)a.aux0);
+}
+
+template <typename T, int NT, int MINB>
+__global__ void __launch_bounds__(NT, MINB) mr_persistent(LaunchArgs a) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    Smem<T> &sm = *reinterpret_cast<Smem<T> *>(smem_raw);
+    // tables: once per block
+    {
+        const uint32_t *src = (const uint32_t *)a.tables;
+        uint32_t *dst = (uint32_t *)&sm.tab;
+        for (int i = threadIdx.x; i < (int)(sizeof(Tables<T>) / 4); i += NT) dst[i] = src[i];
+    }
+    for (;;) {
+        if (threadIdx.x == 0) sm.idx = atomicAdd(a.queue, 1);
+        __syncthreads();
+        int idx = sm.idx;
+        if (idx >= a.n) break;
+        load_instance<T>(sm, a.descs[a.order[idx]]);
+        switch (sm.d.nf) {
+        case 1: run_instance<T, 1, NT>(sm, a); break;
+        case 2: run_instance<T, 2, NT>(sm, a); break;
+        default: run_instance<T, 3, NT>(sm, a); break;
+        }
+        store_instance<T>(sm);
+    }
+}
+
+}  // namespace mrg
+
+// One translation unit per (precision, block size) instantiation keeps the
+// build parallel; mr_dispatch.cu routes a launch to the right one.
+#define MRG_INSTANTIATE(T, NT, MINB, TAG)                                                          \
+    int mrg_launch_##TAG(int grid, const mrg::LaunchArgs &a, cudaStream_t s) {                     \
+        mrg::mr_persistent<T, NT, MINB><<<grid, NT, sizeof(mrg::Smem<T>), s>>>(a);                  \
+        return (int)cudaGetLastError();                                                           \
+    }                                                                                             \
+    int mrg_occ_##TAG(int *nb) {                                                                  \
+        return (int)cudaOccupancyMaxActiveBlocksPerMultiprocessor(nb, mrg::mr_persistent<T, NT, MINB>, \
+                                                                   NT, sizeof(mrg::Smem<T>));       \
+    }                                                                                             \
+    size_t mrg_smem_##TAG() { return sizeof(mrg::Smem<T>); }

@@ -1,0 +1,291 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Meshes are compared bit for bit.  Populations: FP64 path within 1e-12
+relative to the oracle (the stream uses per-level-gap reconstruction tables
+while the oracle predicts level by level, so the two differ by rounding
+only).  Lock-step tests re-seed the oracle with the GPU state before every
+step, so each step's decisions are checked on identical inputs; free-running
+tests compare whole trajectories.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from oracle_helpers import leaves_of, oracle_of, params_of, random_graded_tree
+from paper_2102_12163_gb300 import MR_FP32_MIXED, MR_FP64, MRError, workloads as W
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-12
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    import torch
+
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2102_12163_gb300 import capi
+
+    capi.load()
+
+
+def _solver(insts, precision=MR_FP64, block=None):
+    from paper_2102_12163_gb300 import MRLBM
+
+    s = MRLBM(insts, precision=precision, block=block)
+    s.set_initial()
+    return s
+
+
+def gpu_state(s, i=0):
+    """(R, values) of instance i in the oracle's dense layout."""
+    inst = s.instances[i]
+    R = s.tree(i)
+    lv, ix, f = s.leaves(i)
+    off = O.level_offsets(inst.Jmin, inst.Jmax)
+    vals = np.zeros((inst.q, off[inst.Jmax + 1]))
+    cells = np.array([off[l] for l in lv], dtype=np.int64) + ix
+    vals[:, cells] = f
+    return R, vals, (lv, ix, f)
+
+
+def assert_same_leaves(gpu_leaves, o, tol=TOL):
+    lv, ix, f = gpu_leaves
+    olv, oix, of = o.leaves()
+    assert np.array_equal(lv, olv) and np.array_equal(ix, oix), "leaf sets differ"
+    scale = max(1.0, float(np.max(np.abs(of))))
+    err = float(np.max(np.abs(f - of))) / scale if f.size else 0.0
+    assert err <= tol, err
+
+
+PARITY_CASES = [
+    # (name, instance factory)
+    ("adv-periodic-J9", lambda: W.random_smooth(9, W.EQ_ADVECTION, seed=1, eps=1e-3)),
+    ("burgers-copy-J10", lambda: W.random_smooth(10, W.EQ_BURGERS, seed=2, eps=1e-4, bc=W.BC_COPY)),
+    ("sw-copy-J9", lambda: W.random_smooth(9, W.EQ_SW, seed=3, eps=1e-4, bc=W.BC_COPY)),
+    ("euler-periodic-J10", lambda: W.random_smooth(10, W.EQ_EULER, seed=4, eps=3e-4)),
+    ("euler-copy-J11-jmin4", lambda: W.random_smooth(11, W.EQ_EULER, seed=5, eps=1e-4, bc=W.BC_COPY, Jmin=4)),
+    ("adv-config", lambda: W.advection()),
+]
+
+
+@pytest.mark.parametrize("name,make", PARITY_CASES, ids=[c[0] for c in PARITY_CASES])
+def test_initial_state_matches(name, make):
+    inst = make()
+    s = _solver(inst)
+    o = oracle_of(inst)
+    R, _, lvs = gpu_state(s)
+    Ro, _ = o.get_state()
+    assert np.array_equal(R, Ro)
+    assert_same_leaves(lvs, o, tol=0.0)  # same IEEE operations
+
+
+@pytest.mark.parametrize("name,make", PARITY_CASES, ids=[c[0] for c in PARITY_CASES])
+def test_lockstep_parity(name, make):
+    inst = make()
+    s = _solver(inst)
+    o = O.Oracle(params_of(inst))
+    for n in range(12):
+        R, vals, _ = gpu_state(s)
+        o.set_state(R, vals)
+        o.step()
+        s.advance(1)
+        R2, _, lvs = gpu_state(s)
+        Ro, _ = o.get_state()
+        assert np.array_equal(R2, Ro), f"step {n}: mesh differs"
+        assert_same_leaves(lvs, o)
+
+
+@pytest.mark.parametrize("name,make", PARITY_CASES[:4], ids=[c[0] for c in PARITY_CASES[:4]])
+def test_adapt_then_step_equals_advance(name, make):
+    inst = make()
+    a, b = _solver(inst), _solver(inst)
+    for n in range(5):
+        a.adapt()
+        a.lbm_step()
+        b.advance(1)
+    ra, _, la = gpu_state(a)
+    rb, _, lb = gpu_state(b)
+    assert np.array_equal(ra, rb)
+    assert np.array_equal(la[2], lb[2])
+
+
+@pytest.mark.parametrize("name,make", PARITY_CASES, ids=[c[0] for c in PARITY_CASES])
+def test_free_running_parity(name, make):
+    inst = make()
+    s = _solver(inst)
+    o = oracle_of(inst)
+    for n in range(40):
+        o.step()
+        s.advance(1)
+        R, _, lvs = gpu_state(s)
+        Ro, _ = o.get_state()
+        assert np.array_equal(R, Ro), f"step {n}: mesh differs"
+        assert_same_leaves(lvs, o, tol=1e-11)
+    m, res = s.audit()
+    assert np.allclose(m, o.mass(), rtol=1e-12, atol=1e-13)
+    assert res < 1e-12
+
+
+def test_many_steps_in_one_launch():
+    inst = W.burgers(Jmax=11)
+    s = _solver(inst)
+    o = oracle_of(inst)
+    s.advance(60)
+    o.step(60)
+    R, _, lvs = gpu_state(s)
+    assert np.array_equal(R, o.get_state()[0])
+    assert_same_leaves(lvs, o, tol=1e-11)
+    upd, steps, leaves = s.stats()
+    assert steps == 60 and leaves == len(lvs[0])
+
+
+def test_finest_reconstruction_matches():
+    inst = W.random_smooth(10, W.EQ_EULER, seed=8, eps=1e-4, bc=W.BC_COPY)
+    s = _solver(inst)
+    o = oracle_of(inst)
+    s.advance(15)
+    o.step(15)
+    assert np.max(np.abs(s.finest() - o.finest_moments())) < 1e-12
+
+
+@pytest.mark.parametrize("eq", [W.EQ_ADVECTION, W.EQ_BURGERS, W.EQ_SW, W.EQ_EULER])
+def test_zero_threshold_is_the_uniform_scheme(eq):
+    inst = W.random_smooth(8, eq, seed=30 + eq, eps=0.0, bc=W.BC_COPY)
+    s = _solver(inst)
+    p = params_of(inst)
+    F = O.equilibrium(p, inst.m0)
+    for n in range(10):
+        s.advance(1)
+        F = O.uniform_step(p, F)
+    lv, ix, f = s.leaves()
+    assert np.all(lv == inst.Jmax)
+    assert np.max(np.abs(f - F)) < 1e-14
+
+
+EDGE_CASES = [
+    ("single-level", lambda: W.random_smooth(6, W.EQ_BURGERS, seed=11, Jmin=6)),
+    ("two-levels", lambda: W.random_smooth(6, W.EQ_SW, seed=12, Jmin=5, bc=W.BC_COPY)),
+    ("tiny-levels", lambda: W.random_smooth(4, W.EQ_EULER, seed=13, Jmin=2, eps=1e-5)),
+    ("coarsen-all", lambda: W.random_smooth(9, W.EQ_BURGERS, seed=14, eps=10.0)),
+    ("jmin5-copy", lambda: W.random_smooth(10, W.EQ_ADVECTION, seed=15, Jmin=5, bc=W.BC_COPY)),
+    ("deep-J15", lambda: W.random_smooth(15, W.EQ_BURGERS, seed=16, eps=1e-5)),
+]
+
+
+@pytest.mark.parametrize("name,make", EDGE_CASES, ids=[c[0] for c in EDGE_CASES])
+def test_edge_cases_lockstep(name, make):
+    inst = make()
+    s = _solver(inst)
+    o = O.Oracle(params_of(inst))
+    for n in range(6):
+        R, vals, _ = gpu_state(s)
+        o.set_state(R, vals)
+        o.step()
+        s.advance(1)
+        R2, _, lvs = gpu_state(s)
+        assert np.array_equal(R2, o.get_state()[0]), f"step {n}"
+        assert_same_leaves(lvs, o)
+
+
+@pytest.mark.parametrize("seed,bc", [(40, W.BC_PERIODIC), (41, W.BC_COPY)])
+def test_arbitrary_graded_tree_lockstep(seed, bc):
+    """Random graded trees (many level jumps, coarse and fine neighbours)."""
+    rng = np.random.default_rng(seed)
+    inst = W.random_smooth(10, W.EQ_EULER, seed=seed, bc=bc, eps=1e-4)
+    s = _solver(inst)
+    o = O.Oracle(params_of(inst))
+    R = random_graded_tree(inst.Jmin, inst.Jmax, rng, density=0.3, bc=bc)
+    base = O.equilibrium(params_of(inst), np.array([[1.0], [0.1], [2.0]]))[:, :1]
+    vals = base + 0.02 * rng.normal(size=(inst.q, o.S))
+    s.set_state(0, R, vals)
+    o.set_state(R, vals)
+    o.lbm_step()
+    s.lbm_step()
+    _, _, lvs = gpu_state(s)
+    assert_same_leaves(lvs, o)
+    for n in range(4):
+        R, vals, _ = gpu_state(s)
+        o.set_state(R, vals)
+        o.step()
+        s.advance(1)
+        R2, _, lvs = gpu_state(s)
+        assert np.array_equal(R2, o.get_state()[0])
+        assert_same_leaves(lvs, o)
+
+
+def test_batch_matches_individual_oracles():
+    insts = W.batch(n=48, seed=99, Jmax_range=(6, 10))
+    s = _solver(insts, block=256)
+    steps = 10
+    s.advance(steps)
+    for i in range(0, len(insts), 5):
+        o = oracle_of(insts[i])
+        o.step(steps)
+        R, _, lvs = gpu_state(s, i)
+        assert np.array_equal(R, o.get_state()[0]), i
+        assert_same_leaves(lvs, o, tol=1e-11)
+    upd, _, _ = s.stats()
+    assert upd > 0
+
+
+@pytest.mark.parametrize("block", [128, 256, 512, 1024])
+def test_block_sizes_agree(block):
+    insts = W.batch(n=9, seed=7, Jmax_range=(7, 11))
+    ref = _solver(insts, block=256)
+    s = _solver(insts, block=block)
+    ref.advance(8)
+    s.advance(8)
+    for i in range(len(insts)):
+        assert np.array_equal(ref.tree(i), s.tree(i))
+        assert np.array_equal(ref.leaves(i)[2], s.leaves(i)[2])
+
+
+def test_full_size_sod_lockstep_samples():
+    """The largest single instance at its full size (Jmax = 18), in the launch
+    configuration the benchmark uses, checked against the oracle on sampled steps."""
+    inst = W.sod()
+    s = _solver(inst)
+    o = O.Oracle(params_of(inst))
+    for n in range(3):
+        R, vals, _ = gpu_state(s)
+        o.set_state(R, vals)
+        o.step()
+        s.advance(1)
+        R2, _, lvs = gpu_state(s)
+        assert np.array_equal(R2, o.get_state()[0])
+        assert_same_leaves(lvs, o)
+    s.advance(50)
+    R, vals, _ = gpu_state(s)
+    o.set_state(R, vals)
+    o.step()
+    s.advance(1)
+    R2, _, lvs = gpu_state(s)
+    assert np.array_equal(R2, o.get_state()[0])
+    assert_same_leaves(lvs, o)
+
+
+def test_fp32_path_tracks_the_fp64_oracle():
+    inst = W.random_smooth(11, W.EQ_EULER, seed=50, eps=1e-4, bc=W.BC_COPY)
+    s = _solver(inst, precision=MR_FP32_MIXED)
+    o = oracle_of(inst)
+    s.advance(40)
+    o.step(40)
+    err = inst.dx * np.abs(s.finest() - o.finest_moments()).sum(axis=1)
+    assert np.all(err < 1e-4), err
+    m, res = s.audit()
+    assert np.allclose(m, o.mass(), rtol=1e-5)
+
+
+def test_nonfinite_populations_are_reported():
+    inst = W.random_smooth(8, W.EQ_BURGERS, seed=60)
+    s = _solver(inst)
+    R, vals, _ = gpu_state(s)
+    off = O.level_offsets(inst.Jmin, inst.Jmax)
+    vals[0, off[inst.Jmax] + 5] = np.nan
+    s.set_state(0, R, vals)
+    s.advance(1)
+    with pytest.raises(MRError) as ei:
+        s.sync()
+    assert ei.value.code == -4
