@@ -129,12 +129,12 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def make_workload(name: str, rank: int):
+def make_workload(name: str, rank: int, n_batch: int = 4096):
     from paper_2102_12163_gb300 import workloads as W
 
     if name == "batch":
-        insts = W.batch(n=4096, seed=12163 + rank)
-        desc = "batch of 4096 mixed D1Q2 advection/Burgers, D1Q2^2 shallow water, D1Q2^3 Euler; Jmax 8..14; eps 1e-5..1e-2"
+        insts = W.batch(n=n_batch, seed=12163 + rank)
+        desc = f"batch of {n_batch} mixed D1Q2 advection/Burgers, D1Q2^2 shallow water, D1Q2^3 Euler; Jmax 8..14; eps 1e-5..1e-2"
     else:
         insts = [W.CONFIGS[name]()]
         i = insts[0]
@@ -162,19 +162,19 @@ def _oracle_task(args):
     return upd, time.perf_counter() - t0
 
 
-def oracle_throughput(insts, target_s: float = 15.0, warm: int = 2):
+def oracle_throughput(insts, target_s: float = 15.0, warm: int = 4):
     """The oracle as it stands on a bounded sample of the workload, spread over
     the host cores with a spawned process pool; returns (value, cores, sample)."""
     import multiprocessing as mp
     from concurrent.futures import ProcessPoolExecutor
 
     cores = max(1, min(os.cpu_count() or 1, 16))
-    stride = max(1, len(insts) // (4 * cores))
-    sample = insts[::stride][: 4 * cores]
-    # calibrate steps per instance on one instance
-    u, t = _oracle_task((sample[0], warm, 1))
-    per_step = max(t, 1e-4)
-    n = int(max(1, min(64, target_s * cores / (per_step * len(sample)))))
+    stride = max(1, len(insts) // (8 * cores))
+    sample = insts[::stride][: 8 * cores]
+    # calibrate the step cost on a few sampled instances
+    cal = [_oracle_task((i, warm, 1))[1] for i in sample[: min(8, len(sample))]]
+    per_step = max(sum(cal) / len(cal), 1e-5)
+    n = int(max(1, min(2048, target_s * cores / (per_step * len(sample)))))
     ctx = mp.get_context("spawn")
     t0 = time.perf_counter()
     with ProcessPoolExecutor(cores, mp_context=ctx) as ex:
@@ -267,8 +267,9 @@ def e2e(s, steps: int):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=32)
-    ap.add_argument("--warmup", type=int, default=4)
+    ap.add_argument("--steps", type=int, default=512)
+    ap.add_argument("--warmup", type=int, default=16)
+    ap.add_argument("--instances", type=int, default=4096, help="batch size (smaller only for profiling)")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="batch", choices=["batch", "advection", "burgers", "shallow", "sod"])
     ap.add_argument("--block", type=int, default=None)
@@ -279,7 +280,7 @@ def main():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
-    insts, desc = make_workload(args.workload, rank)
+    insts, desc = make_workload(args.workload, rank, args.instances)
     hbm, hbm_src = peaks()
 
     if args.impl == "reference":

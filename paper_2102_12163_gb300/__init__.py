@@ -40,7 +40,7 @@ class MRLBM:
     """
 
     def __init__(self, instances, precision: int = MR_FP64, device: str = "cuda:0", block: int | None = None,
-                 stream=None):
+                 stream=None, block_team_jmax: int | None = None):
         import torch
 
         self.lib = capi.load()
@@ -67,8 +67,9 @@ class MRLBM:
             self.stream = stream if stream is not None else torch.cuda.Stream(self.device)
             # caller-owned workspace (torch allocations are 512-byte aligned)
             self.ws = torch.empty(self.workspace_bytes, dtype=torch.uint8, device=self.device)
-        if block is not None:
-            self.set_block(block)
+        if block is not None or block_team_jmax is not None:
+            self.set_launch(block or (256 if len(self.instances) > 1 else 1024), 0,
+                            -1 if block_team_jmax is None else block_team_jmax)
         capi.check(self.h, self.lib.mr_bind(self.h, ctypes.c_void_p(self.ws.data_ptr()), self.workspace_bytes,
                                             ctypes.c_void_p(self.stream.cuda_stream)))
 
@@ -84,12 +85,10 @@ class MRLBM:
         except Exception:
             pass
 
-    def set_block(self, block: int):
-        """Threads per block (128, 256, 512 or 1024); applies at the next bind."""
-        fn = getattr(self.lib, "mr_set_launch", None)
-        if fn is None:
-            raise MRError(capi.MR_ERR_ARG, "launch shape control not available")
-        capi.check(self.h, fn(self.h, block, 0))
+    def set_launch(self, block: int, grid: int = 0, block_team_jmax: int = -1):
+        """Threads per block (128, 256, 512 or 1024), blocks (0: one resident
+        wave) and the Jmax from which an instance gets a whole block."""
+        capi.check(self.h, self.lib.mr_set_launch(self.h, block, grid, block_team_jmax))
 
     # -- state -------------------------------------------------------------
     def initial_data(self) -> np.ndarray:

@@ -57,6 +57,7 @@ struct mr_ctx {
     cudaStream_t stream = nullptr;
     bool bound = false, initialised = false;
     int block = 0, grid = 0, grid_req = 0, sms = 0;
+    int team_jmax = -1;  // instances with Jmax >= this get a whole block (-1: default)
     long long launches = 0;
     std::string err;
 
@@ -144,12 +145,7 @@ static void layout(mr_ctx *c) {
         h.S = S;
         h.N = N;
         h.m_off = c->m_off[i];
-        // FP32 path: details in FP64 on the levels where eps_l falls below
-        // 2^-16 (about 256 single-precision ulps of an O(1) population)
-        h.fp64_detail_upto = -1;
-        if (c->fp32())
-            for (int l = d.Jmin; l <= d.Jmax; ++l)
-                if (std::ldexp(d.eps, l - d.Jmax) < std::ldexp(1.0, -16)) h.fp64_detail_upto = l;
+        h.team = 1;
         c->inst_off[i] = o;
         size_t vb = c->vbytes();
         size_t oV = 0, oPhi = align_up(oV + vb * q * S), oM = align_up(oPhi + vb * q * (N + 1));
@@ -368,13 +364,25 @@ mr_status mr_bind(mr_ctx *c, void *ws, size_t bytes, void *stream) {
         dd[i].lists = (uint32_t *)(base + (size_t)dd[i].lists);
         dd[i].st = (InstState *)(c->ws + c->off_state) + i;
     }
+    // launch shape: one block per instance; 1024 threads for a lone large instance
+    if (c->block == 0) {
+        int jmax = 0;
+        for (auto &d : c->desc) jmax = std::max(jmax, d.Jmax);
+        c->block = n == 1 ? (jmax >= 12 ? 1024 : 512) : 256;
+    }
+    // team per instance: a whole block from team_jmax on (a lone instance always
+    // gets the block), one warp below
+    int tj = c->team_jmax >= 0 ? c->team_jmax : 13;
+    for (int i = 0; i < n; ++i) dd[i].team = (n == 1 || c->desc[i].Jmax >= tj) ? 1 : 0;
     c->hdesc = dd;
-    // processing order: largest instances first (q 2^Jmax as the cost estimate)
+    // processing order: block-team instances first, each group largest first
+    // (nf 2^Jmax as the cost estimate); the kernel relies on the grouping
     std::vector<int> order(n), ident(n);
     for (int i = 0; i < n; ++i) order[i] = ident[i] = i;
     std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
-        double cx = (double)c->hdesc[x].nf * std::ldexp(1.0, c->hdesc[x].Jmax);
-        double cy = (double)c->hdesc[y].nf * std::ldexp(1.0, c->hdesc[y].Jmax);
+        if (dd[x].team != dd[y].team) return dd[x].team > dd[y].team;
+        double cx = (double)dd[x].nf * std::ldexp(1.0, dd[x].Jmax);
+        double cy = (double)dd[y].nf * std::ldexp(1.0, dd[y].Jmax);
         return cx > cy;
     });
     Tables<double> td;
@@ -392,12 +400,6 @@ mr_status mr_bind(mr_ctx *c, void *ws, size_t bytes, void *stream) {
     if ((rc = c->cuda(cudaMemcpyAsync(c->ws + c->off_tab + sizeof td, &tf, sizeof tf, cudaMemcpyHostToDevice, s), "upload")))
         return (mr_status)rc;
     if ((rc = c->cuda(cudaStreamSynchronize(s), "cudaStreamSynchronize"))) return (mr_status)rc;
-    // launch shape: one block per instance; 1024 threads for a lone large instance
-    if (c->block == 0) {
-        int jmax = 0;
-        for (auto &d : c->desc) jmax = std::max(jmax, d.Jmax);
-        c->block = n == 1 ? (jmax >= 12 ? 1024 : 512) : 256;
-    }
     int nb = 0;
     if ((rc = c->cuda((cudaError_t)mrg_occupancy(c->fp32(), c->block, &nb), "occupancy"))) return (mr_status)rc;
     c->grid = c->grid_req > 0 ? c->grid_req : std::max(1, nb) * c->sms;
@@ -649,13 +651,16 @@ mr_status mr_stats(mr_ctx *c, unsigned long long *updates, unsigned long long *s
     return MR_OK;
 }
 
-mr_status mr_set_launch(mr_ctx *c, int block, int grid) {
+mr_status mr_set_launch(mr_ctx *c, int block, int grid, int block_team_jmax) {
     if (!c) return MR_ERR_ARG;
     if (block != 128 && block != 256 && block != 512 && block != 1024)
         return (mr_status)c->fail(MR_ERR_ARG, "block must be 128, 256, 512 or 1024");
     if (grid < 0) return (mr_status)c->fail(MR_ERR_ARG, "grid must be >= 0");
+    if (c->bound && block_team_jmax != c->team_jmax && block_team_jmax >= 0)
+        return (mr_status)c->fail(MR_ERR_STATE, "team threshold must be set before mr_bind");
     c->block = block;
     c->grid_req = grid;
+    if (block_team_jmax >= 0) c->team_jmax = block_team_jmax;
     if (c->bound) {
         int nb = 0;
         int rc = c->cuda((cudaError_t)mrg_occupancy(c->fp32(), c->block, &nb), "occupancy");

@@ -1,9 +1,12 @@
 // mr_kernels.cuh -- sm_103a kernels of the multiresolution-adaptive lattice
 // Boltzmann step (Bellotti, Gouarin, Graille, Massot, arXiv 2102.12163).
 //
-// One thread block owns one instance at a time and runs every phase of the
-// step on it, separated by block barriers; blocks pull instances from an
-// atomic work queue (persistent launch).  Inside a step:
+// A "team" owns one instance at a time and runs every phase of the step on it:
+// either a whole thread block (large instances; block barriers between phases)
+// or a single warp (small instances; warp barriers only, eight instances in
+// flight per block).  Blocks pull instances from an atomic work queue sorted
+// largest first; a block that meets a warp-team instance switches to warp mode
+// and its warps pull the rest of the queue independently.  Inside a step:
 //
 //   adapt (Section 4.1)
 //     A1  projection up the current tree (Def. Projection operator)
@@ -12,7 +15,7 @@
 //     A3  enlargement H: same-level dilation and children of REF pairs
 //     A4  grading G, sweeping fine to coarse over bitmask words (Def. Graded
 //         tree), fused with the leaf / transfer / ghost marking
-//     A5  list compaction: popcount + block prefix scan over the mask words
+//     A5  list compaction: popcount + prefix scan over the mask words
 //     A6  data transfer: prediction of the new cells, coarse to fine
 //   step (Sections 4.3, 4.5)
 //     S1  leaves collision (eq. LeavesCollision)
@@ -35,6 +38,7 @@
 namespace mrg {
 
 constexpr double C1 = -0.125;  // prediction coefficient c_1 for gamma = 1 (Section 3.1)
+constexpr unsigned FULL = 0xFFFFFFFFu;
 
 // ---------------------------------------------------------------------------
 // arithmetic: the FP64 path uses explicitly rounded operations (never fused)
@@ -148,17 +152,16 @@ __device__ __forceinline__ uint32_t dilate(Get get, int l, int wi, int r, int bc
 }
 
 // ---------------------------------------------------------------------------
-// shared memory
+// shared memory: per-team state and per-block tables
 
 template <typename T>
-struct Smem {
-    Tables<T> tab;
+struct TeamSmem {
     InstDesc d;
     int woff[MAXLEV + 2];
     int seg[NLIST][MAXLEV + 2];
-    int scan_w[NLIST][32];
+    double eps_l[MAXLEV + 1], big_l[MAXLEV + 1], dx_l[MAXLEV + 1];  // per level
+    float eps_f[MAXLEV + 1], big_f[MAXLEV + 1];
     int scan_tot[NLIST];
-    double red[3][32];
     double mass[3];
     double audit;
     unsigned long long updates, steps;
@@ -167,8 +170,22 @@ struct Smem {
     int g0s, gbase;  // level_of_word constants
 };
 
+// block-team scratch (scan partials and reduction slots of the warps)
+struct BlockScratch {
+    int scan_w[NLIST][32];
+    double red[3][32];
+};
+
+template <typename T, int NT>
+struct BlockSmem {
+    Tables<T> tab;
+    BlockScratch scratch;
+    TeamSmem<T> team[NT / 32];
+    int idx;
+};
+
 template <typename T>
-__device__ __forceinline__ void level_of_word(const Smem<T> &sm, int g, int &l, int &wi) {
+__device__ __forceinline__ void level_of_word(const TeamSmem<T> &sm, int g, int &l, int &wi) {
     if (g < sm.g0s) {
         l = sm.d.Jmin + g;
         wi = 0;
@@ -250,27 +267,53 @@ __device__ __forceinline__ T predict(const T *row, long long p, int odd, int lp,
 }
 
 // ---------------------------------------------------------------------------
-// the instance worker
+// the instance worker; TS threads (a warp or the whole block) form the team
 
-template <typename T, int NF, int NT>
+template <typename T, int NF, int TS>
 struct Worker {
     static constexpr int Q = 2 * NF;
-    Smem<T> &sm;
+    static constexpr bool WARP = TS == 32;
+    TeamSmem<T> &sm;
+    const Tables<T> &tab;
+    BlockScratch &bx;
     const InstDesc &d;
     T *V;
     T *Phi;
     uint32_t *M;  // mask base
-    int tid;
+    int tid;      // rank in the team
 
-    __device__ Worker(Smem<T> &s) : sm(s), d(s.d), tid(threadIdx.x) {
+    __device__ Worker(TeamSmem<T> &s, const Tables<T> &tb, BlockScratch &x, int rank)
+        : sm(s), tab(tb), bx(x), d(s.d), tid(rank) {
         V = (T *)d.V;
         Phi = (T *)d.Phi;
         M = d.masks;
     }
 
+    __device__ __forceinline__ void sync() const {
+        if constexpr (WARP)
+            __syncwarp();
+        else
+            __syncthreads();
+    }
+
     __device__ __forceinline__ uint32_t *mask(int m) { return M + (long long)m * d.Wtot; }
     __device__ __forceinline__ uint32_t *list(int L) { return d.lists + d.list_off[L]; }
     __device__ __forceinline__ T *row(int h, int l) { return V + (long long)h * d.S + cell_off(l, d.Jmin); }
+
+    // sum over the team of a per-thread double
+    __device__ __forceinline__ double team_sum(double x, int j) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(FULL, x, o);
+        if constexpr (WARP) {
+            return __shfl_sync(FULL, x, 0);
+        } else {
+            if ((tid & 31) == 0) bx.red[j][tid >> 5] = x;
+            sync();
+            double t = 0.0;
+            for (int w = 0; w < TS / 32; ++w) t += bx.red[j][w];
+            return t;
+        }
+    }
 
     // ---- A1 / S2: projection up the tree over the internal cells ----------
     __device__ void upsweep() {
@@ -278,7 +321,7 @@ struct Worker {
         for (int l = d.Jmax - 1; l >= d.Jmin; --l) {
             int b = sm.seg[L_INT][l], e = sm.seg[L_INT][l + 1];
             if (b == e) continue;
-            for (int i = b + tid; i < e; i += NT) {
+            for (int i = b + tid; i < e; i += TS) {
                 long long k = lst[i] & KMASK;
 #pragma unroll
                 for (int h = 0; h < Q; ++h) {
@@ -286,43 +329,74 @@ struct Worker {
                     row(h, l)[k] = T(0.5) * (c.x + c.y);
                 }
             }
-            __syncthreads();
+            sync();
         }
     }
 
     // ---- A2: details, threshold T, Harten flags ----------------------------
+    // FP64: the detail of Section 3.2 in double.  FP32: the detail in float with
+    // a rigorous bound on its rounding error; only when a threshold lies within
+    // that bound is the detail recomputed in FP64 from the stored values, so
+    // every decision equals the one the exact detail of the stored state gives.
     __device__ void details() {
         const uint32_t *lst = list(L_EVEN);
         int b = sm.seg[L_EVEN][d.Jmin + 1], e = sm.seg[L_EVEN][d.Jmax + 1];
         uint32_t *keep = mask(M_KEEP), *ref = mask(M_REF);
-        for (int i = b + tid; i < e; i += NT) {
+        for (int i = b + tid; i < e; i += TS) {
             uint32_t ent = lst[i];
             int l = ent >> KBITS;
             long long k = ent & KMASK, p = k >> 1;
-            double D = 0.0;
-            bool wide = sizeof(T) == 8 || l <= d.fp64_detail_upto;
+            long long pl = wrapc(p - 1, l - 1, d.bc), pr = wrapc(p + 1, l - 1, d.bc);
+            bool keepit, refit, tie = false;
+            const bool hasref = l < d.Jmax;
+            if constexpr (sizeof(T) == 8) {
+                double D = 0.0;
 #pragma unroll
-            for (int h = 0; h < Q; ++h) {
-                const T *rc = row(h, l - 1);
-                double dv;
-                if (wide) {
-                    double vl = (double)rc[wrapc(p - 1, l - 1, d.bc)], vp = (double)rc[p],
-                           vr = (double)rc[wrapc(p + 1, l - 1, d.bc)];
-                    dv = (double)row(h, l)[k] - (vp + C1 * (vr - vl));
-                } else {
-                    dv = (double)(row(h, l)[k] - predict<T>(rc, p, 0, l - 1, d.bc));
+                for (int h = 0; h < Q; ++h) {
+                    const T *rc = row(h, l - 1);
+                    double dv = row(h, l)[k] - (rc[p] + C1 * (rc[pr] - rc[pl]));
+                    D = fmax(D, fabs(dv));
                 }
-                D = fmax(D, fabs(dv));
+                double el = sm.eps_l[l], bl = sm.big_l[l];
+                keepit = D >= el;
+                refit = hasref && D >= bl;
+                tie = fabs(D - el) <= 1e-12 * el || (hasref && fabs(D - bl) <= 1e-12 * bl);
+            } else {
+                float D = 0.0f, B = 0.0f;
+#pragma unroll
+                for (int h = 0; h < Q; ++h) {
+                    const T *rc = row(h, l - 1);
+                    float vk = row(h, l)[k], vl = rc[pl], vp = rc[p], vr = rc[pr];
+                    float dv = vk - (vp + float(C1) * (vr - vl));
+                    D = fmaxf(D, fabsf(dv));
+                    B = fmaxf(B, fabsf(vk) + fabsf(vp) + fabsf(vl) + fabsf(vr));
+                }
+                B *= 0x1p-21f;  // 4 times the rounding bound of the detail evaluation
+                float el = sm.eps_f[l], bl = sm.big_f[l];
+                // the band also covers the rounding of the thresholds to float
+                bool amb = fabsf(D - el) <= B + el * 0x1p-22f || (hasref && fabsf(D - bl) <= B + bl * 0x1p-22f);
+                if (amb) {
+                    double Dd = 0.0;
+                    for (int h = 0; h < Q; ++h) {
+                        const T *rc = row(h, l - 1);
+                        double dv = (double)row(h, l)[k] - ((double)rc[p] + C1 * ((double)rc[pr] - (double)rc[pl]));
+                        Dd = fmax(Dd, fabs(dv));
+                    }
+                    double e64 = sm.eps_l[l], b64 = sm.big_l[l];
+                    keepit = Dd >= e64;
+                    refit = hasref && Dd >= b64;
+                    tie = fabs(Dd - e64) <= 1e-12 * e64 || (hasref && fabs(Dd - b64) <= 1e-12 * b64);
+                } else {
+                    keepit = D >= el;
+                    refit = hasref && D >= bl;
+                }
             }
-            double eps_l = ldexp(d.eps, l - d.Jmax);
-            double big = ldexp(eps_l, d.mu_bar + 1);
-            int w = (int)(k >> 5);
-            uint32_t bits = 3u << (k & 31);
-            if (fabs(D - eps_l) <= 1e-12 * eps_l || (l < d.Jmax && fabs(D - big) <= 1e-12 * big))
-                atomicAdd(&sm.near_ties, 1);
-            if (D >= eps_l) {
+            if (tie) atomicAdd(&sm.near_ties, 1);
+            if (keepit) {
+                int w = (int)(k >> 5);
+                uint32_t bits = 3u << (k & 31);
                 atomicOr(&keep[sm.woff[l] + w], bits);
-                if (l < d.Jmax && D >= big) atomicOr(&ref[sm.woff[l] + w], bits);
+                if (refit) atomicOr(&ref[sm.woff[l] + w], bits);
             }
         }
     }
@@ -330,7 +404,7 @@ struct Worker {
     // ---- A3: R(H(T)) per word ------------------------------------------------
     __device__ void enlarge(uint32_t *Rn) {
         const uint32_t *keep = mask(M_KEEP), *ref = mask(M_REF);
-        for (int g = tid; g < d.Wtot; g += NT) {
+        for (int g = tid; g < d.Wtot; g += TS) {
             int l, wi;
             level_of_word(sm, g, l, wi);
             uint32_t vb = valid_bits(l), rh;
@@ -350,6 +424,7 @@ struct Worker {
     // grade = false only re-derives the marks of a tree known to be graded.
     __device__ void grade_and_mark(uint32_t *Rn, const uint32_t *Ro, bool grade) {
         uint32_t *LF = mask(M_LEAF), *PR = mask(M_PRED), *GH = mask(M_GH);
+        uint32_t *keep = mask(M_KEEP), *ref = mask(M_REF);
         for (int l = d.Jmax; l >= d.Jmin; --l) {
             const uint32_t *rl = Rn + sm.woff[l];
             const uint32_t *rf = l < d.Jmax ? Rn + sm.woff[l + 1] : nullptr;
@@ -358,7 +433,7 @@ struct Worker {
                 uint32_t *rp = Rn + sm.woff[l - 1];
                 int Wp = nwords(l - 1);
                 uint32_t vb = valid_bits(l - 1);
-                for (int wp = tid; wp < Wp; wp += NT)
+                for (int wp = tid; wp < Wp; wp += TS)
                     rp[wp] |= pairexpand(dilate([&](int j) { return fold_at(rl, l, j); }, l - 1, wp, 1, d.bc)) & vb;
             }
             int W = nwords(l);
@@ -366,7 +441,7 @@ struct Worker {
             const uint32_t *pf = l < d.Jmax ? PR + sm.woff[l + 1] : nullptr;
             const uint32_t *gf = l < d.Jmax ? GH + sm.woff[l + 1] : nullptr;
             auto leafw = [&](int j) { return rf ? (rl[j] & ~fold_at(rf, l + 1, j)) : rl[j]; };
-            for (int wi = tid; wi < W; wi += NT) {
+            for (int wi = tid; wi < W; wi += TS) {
                 uint32_t lf = leafw(wi);
                 uint32_t ro = Ro[sm.woff[l] + wi];
                 uint32_t pr = lf & ~ro, gh = 0;
@@ -377,13 +452,16 @@ struct Worker {
                 LF[sm.woff[l] + wi] = lf & vb;
                 PR[sm.woff[l] + wi] = pr & vb;
                 GH[sm.woff[l] + wi] = gh & ~rl[wi] & vb;
+                // KEEP / REF of this level were last read by enlarge: clear for the next step
+                keep[sm.woff[l] + wi] = 0u;
+                ref[sm.woff[l] + wi] = 0u;
             }
-            __syncthreads();
+            sync();
         }
     }
 
     // ---- A5: list compaction -------------------------------------------------
-    __device__ void block_scan(int (&v)[NLIST], int (&excl)[NLIST]) {
+    __device__ void team_scan(int (&v)[NLIST], int (&excl)[NLIST]) {
         int lane = tid & 31, warp = tid >> 5;
         int inc[NLIST];
 #pragma unroll
@@ -391,29 +469,41 @@ struct Worker {
             int x = v[L];
 #pragma unroll
             for (int o = 1; o < 32; o <<= 1) {
-                int y = __shfl_up_sync(0xFFFFFFFFu, x, o);
+                int y = __shfl_up_sync(FULL, x, o);
                 if (lane >= o) x += y;
             }
             inc[L] = x;
-            if (lane == 31) sm.scan_w[L][warp] = x;
         }
-        __syncthreads();
-        if (warp == 0) {
+        if constexpr (WARP) {
 #pragma unroll
             for (int L = 0; L < NLIST; ++L) {
-                int x0 = lane < NT / 32 ? sm.scan_w[L][lane] : 0, x = x0;
-#pragma unroll
-                for (int o = 1; o < 32; o <<= 1) {
-                    int y = __shfl_up_sync(0xFFFFFFFFu, x, o);
-                    if (lane >= o) x += y;
-                }
-                sm.scan_w[L][lane] = x - x0;
-                if (lane == 31) sm.scan_tot[L] = x;
+                excl[L] = inc[L] - v[L];
+                int tot = __shfl_sync(FULL, inc[L], 31);
+                if (lane == 0) sm.scan_tot[L] = tot;
             }
-        }
-        __syncthreads();
+            __syncwarp();
+        } else {
 #pragma unroll
-        for (int L = 0; L < NLIST; ++L) excl[L] = sm.scan_w[L][warp] + inc[L] - v[L];
+            for (int L = 0; L < NLIST; ++L)
+                if (lane == 31) bx.scan_w[L][warp] = inc[L];
+            sync();
+            if (warp == 0) {
+#pragma unroll
+                for (int L = 0; L < NLIST; ++L) {
+                    int x0 = lane < TS / 32 ? bx.scan_w[L][lane] : 0, x = x0;
+#pragma unroll
+                    for (int o = 1; o < 32; o <<= 1) {
+                        int y = __shfl_up_sync(FULL, x, o);
+                        if (lane >= o) x += y;
+                    }
+                    bx.scan_w[L][lane] = x - x0;
+                    if (lane == 31) sm.scan_tot[L] = x;
+                }
+            }
+            sync();
+#pragma unroll
+            for (int L = 0; L < NLIST; ++L) excl[L] = bx.scan_w[L][warp] + inc[L] - v[L];
+        }
     }
 
     __device__ __forceinline__ void word_lists(const uint32_t *Rn, int g, int l, uint32_t (&m)[NLIST]) {
@@ -426,7 +516,7 @@ struct Worker {
     }
 
     __device__ void build_lists(const uint32_t *Rn) {
-        int C = (d.Wtot + NT - 1) / NT;
+        int C = (d.Wtot + TS - 1) / TS;
         int g0 = tid * C, g1 = min(d.Wtot, g0 + C);
         int cnt[NLIST] = {0, 0, 0, 0, 0}, off[NLIST];
         for (int g = g0; g < g1; ++g) {
@@ -437,7 +527,7 @@ struct Worker {
 #pragma unroll
             for (int L = 0; L < NLIST; ++L) cnt[L] += __popc(m[L]);
         }
-        block_scan(cnt, off);
+        team_scan(cnt, off);
         for (int g = g0; g < g1; ++g) {
             int l, wi;
             level_of_word(sm, g, l, wi);
@@ -457,12 +547,13 @@ struct Worker {
                 }
             }
         }
+        sync();
         if (tid == 0) {
 #pragma unroll
             for (int L = 0; L < NLIST; ++L) sm.seg[L][d.Jmax + 1] = sm.scan_tot[L];
             sm.nleaf = sm.scan_tot[L_LEAF];
         }
-        __syncthreads();
+        sync();
     }
 
     // ---- A6 / S3: prediction of listed cells, coarse to fine -----------------
@@ -471,29 +562,24 @@ struct Worker {
         for (int l = d.Jmin + 1; l <= d.Jmax; ++l) {
             int b = sm.seg[L][l], e = sm.seg[L][l + 1];
             if (b == e) continue;
-            for (int i = b + tid; i < e; i += NT) {
+            for (int i = b + tid; i < e; i += TS) {
                 long long k = lst[i] & KMASK;
 #pragma unroll
                 for (int h = 0; h < Q; ++h) row(h, l)[k] = predict<T>(row(h, l - 1), k >> 1, (int)(k & 1), l - 1, d.bc);
             }
-            __syncthreads();
+            sync();
         }
     }
 
     // ---- mesh adaptation ----------------------------------------------------
     __device__ void adapt() {
         uint32_t *Ro = mask(sm.cur), *Rn = mask(sm.cur ^ 1);
-        uint32_t *keep = mask(M_KEEP), *ref = mask(M_REF);
-        for (int g = tid; g < d.Wtot; g += NT) {
-            keep[g] = 0u;
-            ref[g] = 0u;
-        }
-        upsweep();  // ends with a barrier unless no level has internal cells
-        __syncthreads();
+        upsweep();
+        sync();
         details();
-        __syncthreads();
+        sync();
         enlarge(Rn);
-        __syncthreads();
+        sync();
         grade_and_mark(Rn, Ro, true);
         build_lists(Rn);
         predict_fill(L_PRED);
@@ -501,7 +587,7 @@ struct Worker {
             sm.cur ^= 1;
             sm.updates += (unsigned long long)sm.nleaf;
         }
-        __syncthreads();
+        sync();
     }
 
     // ---- one step of the adaptive scheme on the current mesh -----------------
@@ -509,7 +595,7 @@ struct Worker {
         const uint32_t *leaves = list(L_LEAF);
         int nl = sm.nleaf;
         // S1 leaves collision
-        for (int i = tid; i < nl; i += NT) {
+        for (int i = tid; i < nl; i += TS) {
             uint32_t ent = leaves[i];
             int l = ent >> KBITS;
             long long k = ent & KMASK;
@@ -520,11 +606,11 @@ struct Worker {
 #pragma unroll
             for (int h = 0; h < Q; ++h) row(h, l)[k] = f[h];
         }
-        __syncthreads();
+        sync();
         upsweep();             // S2
         predict_fill(L_GH);    // S3
         reconstruct_edges();   // S4
-        __syncthreads();
+        sync();
         stream_and_audit();    // S5
     }
 
@@ -534,7 +620,7 @@ struct Worker {
         const uint32_t *R = mask(sm.cur);
         const long long N = d.N;
         const int bc = d.bc;
-        for (int i = tid; i < sm.nleaf; i += NT) {
+        for (int i = tid; i < sm.nleaf; i += TS) {
             uint32_t ent = leaves[i];
             int l = ent >> KBITS;
             long long k = ent & KMASK;
@@ -553,7 +639,7 @@ struct Worker {
                     fin_r = (rf[c >> 5] >> (c & 31)) & 1u;
                 }
             }
-            const T *cf = sm.tab.cf[dj], *t1 = sm.tab.t1[dj], *bf = sm.tab.bf[dj];
+            const T *cf = tab.cf[dj], *t1 = tab.t1[dj], *bf = tab.bf[dj];
 #pragma unroll
             for (int h = 0; h < Q; ++h) {
                 const T *r = row(h, l);
@@ -628,69 +714,63 @@ struct Worker {
 #pragma unroll
         for (int j = 0; j < NF; ++j) macc[j] = 0.0;
         bool bad = false;
-        for (int i = tid; i < sm.nleaf; i += NT) {
+        for (int i = tid; i < sm.nleaf; i += TS) {
             uint32_t ent = leaves[i];
             int l = ent >> KBITS;
             long long k = ent & KMASK;
             int dj = d.Jmax - l;
             long long first = k << dj, next = (k + 1) << dj;
             if (d.bc == 0) next &= N - 1;
-            double dx = ldexp(d.b - d.a, -l);
+            const T w = (T)ldexpf(1.0f, -dj);
             T fn[Q];
 #pragma unroll
             for (int h = 0; h < Q; ++h) {
                 const T *ph = Phi + (long long)h * (N + 1);
-                T coef = (h & 1) ? -ldexpf(1.0f, -dj) : ldexpf(1.0f, -dj);
+                T coef = (h & 1) ? -w : w;
                 T *r = row(h, l);
                 T v = r[k] + coef * (ph[first] - ph[next]);
                 bad |= !isfinite(v);
                 r[k] = v;
                 fn[h] = v;
             }
+            const double dx = sm.dx_l[l];
 #pragma unroll
             for (int j = 0; j < NF; ++j) macc[j] += dx * ((double)fn[2 * j] + (double)fn[2 * j + 1]);
         }
-        // block reduction of the FP64 totals
-        int lane = tid & 31, warp = tid >> 5;
-#pragma unroll
-        for (int j = 0; j < NF; ++j) {
-            double x = macc[j];
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xFFFFFFFFu, x, o);
-            if (lane == 0) sm.red[j][warp] = x;
-        }
         if (bad) atomicOr(&sm.status, (int)ST_NONFINITE);
-        __syncthreads();
+        double tot[NF];
+#pragma unroll
+        for (int j = 0; j < NF; ++j) tot[j] = team_sum(macc[j], j);
         if (tid == 0) {
-            double dxJ = ldexp(d.b - d.a, -d.Jmax);
+            double dxJ = sm.dx_l[d.Jmax];
             for (int j = 0; j < NF; ++j) {
-                double tot = 0.0;
-                for (int w = 0; w < NT / 32; ++w) tot += sm.red[j][w];
                 double flux = 0.0;
                 if (d.bc == 1) {
                     const T *pp = Phi + (long long)(2 * j) * (N + 1), *pm = Phi + (long long)(2 * j + 1) * (N + 1);
                     flux = dxJ * (((double)pp[0] - (double)pp[N]) - ((double)pm[0] - (double)pm[N]));
                 }
-                double res = fabs(tot - sm.mass[j] - flux);
+                double res = fabs(tot[j] - sm.mass[j] - flux);
                 sm.audit = fmax(sm.audit, res);
-                sm.mass[j] = tot;
+                sm.mass[j] = tot[j];
             }
             sm.steps += 1ULL;
         }
-        __syncthreads();
+        sync();
     }
 
     // ---- initial state -------------------------------------------------------
     // full tree, populations at equilibrium of the conserved moments (staged m_cons)
     __device__ void init_full(const double *mcons) {
         uint32_t *R = mask(M_R0);
-        for (int g = tid; g < d.Wtot; g += NT) {
+        for (int g = tid; g < d.Wtot; g += TS) {
             int l, wi;
             level_of_word(sm, g, l, wi);
             R[g] = valid_bits(l);
+            mask(M_KEEP)[g] = 0u;
+            mask(M_REF)[g] = 0u;
         }
         const long long N = d.N;
-        for (long long k = tid; k < N; k += NT) {
+        for (long long k = tid; k < N; k += TS) {
             double mc[NF], f[Q];
 #pragma unroll
             for (int j = 0; j < NF; ++j) mc[j] = mcons[j * N + k];
@@ -699,14 +779,14 @@ struct Worker {
             for (int h = 0; h < Q; ++h) row(h, d.Jmax)[k] = (T)f[h];
         }
         if (tid == 0) sm.cur = M_R0;
-        __syncthreads();
+        sync();
         finish_init();
     }
 
     // arbitrary graded tree (one byte per cell) and values
     __device__ void init_state(const unsigned char *Rb, const double *vals) {
         uint32_t *R = mask(M_R0);
-        for (int g = tid; g < d.Wtot; g += NT) {
+        for (int g = tid; g < d.Wtot; g += TS) {
             int l, wi;
             level_of_word(sm, g, l, wi);
             long long base = cell_off(l, d.Jmin) + 32LL * wi;
@@ -714,10 +794,12 @@ struct Worker {
             uint32_t w = 0;
             for (int b = 0; b < nb; ++b) w |= (Rb[base + b] ? 1u : 0u) << b;
             R[g] = w;
+            mask(M_KEEP)[g] = 0u;
+            mask(M_REF)[g] = 0u;
         }
-        for (long long c = tid; c < (long long)Q * d.S; c += NT) V[c] = (T)vals[c];
+        for (long long c = tid; c < (long long)Q * d.S; c += TS) V[c] = (T)vals[c];
         if (tid == 0) sm.cur = M_R0;
-        __syncthreads();
+        sync();
         finish_init();
     }
 
@@ -730,65 +812,55 @@ struct Worker {
         double macc[NF];
 #pragma unroll
         for (int j = 0; j < NF; ++j) macc[j] = 0.0;
-        for (int i = tid; i < sm.nleaf; i += NT) {
+        for (int i = tid; i < sm.nleaf; i += TS) {
             uint32_t ent = leaves[i];
             int l = ent >> KBITS;
             long long k = ent & KMASK;
-            double dx = ldexp(d.b - d.a, -l);
+            double dx = sm.dx_l[l];
 #pragma unroll
             for (int j = 0; j < NF; ++j) macc[j] += dx * ((double)row(2 * j, l)[k] + (double)row(2 * j + 1, l)[k]);
         }
-        int lane = tid & 31, warp = tid >> 5;
+        double tot[NF];
 #pragma unroll
-        for (int j = 0; j < NF; ++j) {
-            double x = macc[j];
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xFFFFFFFFu, x, o);
-            if (lane == 0) sm.red[j][warp] = x;
-        }
-        __syncthreads();
+        for (int j = 0; j < NF; ++j) tot[j] = team_sum(macc[j], j);
         if (tid == 0) {
-            for (int j = 0; j < NF; ++j) {
-                double tot = 0.0;
-                for (int w = 0; w < NT / 32; ++w) tot += sm.red[j][w];
-                sm.mass[j] = tot;
-            }
+            for (int j = 0; j < NF; ++j) sm.mass[j] = tot[j];
             sm.audit = 0.0;
             sm.status = 0;
             sm.near_ties = 0;
             sm.updates = 0ULL;
             sm.steps = 0ULL;
         }
-        __syncthreads();
+        sync();
     }
 
     // ---- multiresolution reconstruction on the finest level (measurement) ----
     __device__ void finest(double *out) {
         upsweep();
-        __syncthreads();
+        sync();
         const uint32_t *R = mask(sm.cur);
         for (int l = d.Jmin + 1; l <= d.Jmax; ++l) {
             long long n = 1LL << l;
             const uint32_t *rl = R + sm.woff[l];
-            for (long long k = tid; k < n; k += NT)
+            for (long long k = tid; k < n; k += TS)
                 if (!((rl[k >> 5] >> (k & 31)) & 1u))
 #pragma unroll
                     for (int h = 0; h < Q; ++h) row(h, l)[k] = predict<T>(row(h, l - 1), k >> 1, (int)(k & 1), l - 1, d.bc);
-            __syncthreads();
+            sync();
         }
         const long long N = d.N;
-        for (long long k = tid; k < N; k += NT)
+        for (long long k = tid; k < N; k += TS)
 #pragma unroll
             for (int j = 0; j < NF; ++j) out[j * N + k] = (double)row(2 * j, d.Jmax)[k] + (double)row(2 * j + 1, d.Jmax)[k];
-        __syncthreads();
+        sync();
     }
 };
 
 // ---------------------------------------------------------------------------
+// instance state in and out of shared memory (TS threads of the team)
 
-template <typename T>
-__device__ void load_instance(Smem<T> &sm, const InstDesc &dg) {
-    int tid = threadIdx.x;
+template <typename T, int TS>
+__device__ void load_instance(TeamSmem<T> &sm, const InstDesc &dg, int tid) {
     if (tid == 0) {
         sm.d = dg;
         const InstState &st = *dg.st;
@@ -810,13 +882,25 @@ __device__ void load_instance(Smem<T> &sm, const InstDesc &dg) {
         sm.g0s = Jmin < 5 ? 5 - Jmin : 0;
         sm.gbase = Jmin < 5 ? 1 : (1 << (Jmin - 5));
     }
-    for (int i = tid; i < NLIST * (MAXLEV + 2); i += blockDim.x) (&sm.seg[0][0])[i] = (&dg.st->seg[0][0])[i];
-    __syncthreads();
+    for (int l = tid; l <= MAXLEV; l += TS) {
+        // eps_l = 2^{l - Jmax} eps (Prop. ErrorControl), Harten level 2^{mu_bar + 1} eps_l
+        double el = ldexp(dg.eps, l - dg.Jmax);
+        double bl = ldexp(el, dg.mu_bar + 1);
+        sm.eps_l[l] = el;
+        sm.big_l[l] = bl;
+        sm.eps_f[l] = (float)el;
+        sm.big_f[l] = (float)bl;
+        sm.dx_l[l] = ldexp(dg.b - dg.a, -l);
+    }
+    for (int i = tid; i < NLIST * (MAXLEV + 2); i += TS) (&sm.seg[0][0])[i] = (&dg.st->seg[0][0])[i];
+    if constexpr (TS == 32)
+        __syncwarp();
+    else
+        __syncthreads();
 }
 
-template <typename T>
-__device__ void store_instance(Smem<T> &sm) {
-    int tid = threadIdx.x;
+template <typename T, int TS>
+__device__ void store_instance(TeamSmem<T> &sm, int tid) {
     InstState &st = *sm.d.st;
     if (tid == 0) {
         st.cur = sm.cur;
@@ -828,13 +912,16 @@ __device__ void store_instance(Smem<T> &sm) {
         st.audit = sm.audit;
         for (int j = 0; j < 3; ++j) st.mass[j] = sm.mass[j];
     }
-    for (int i = tid; i < NLIST * (MAXLEV + 2); i += blockDim.x) (&st.seg[0][0])[i] = (&sm.seg[0][0])[i];
-    __syncthreads();
+    for (int i = tid; i < NLIST * (MAXLEV + 2); i += TS) (&st.seg[0][0])[i] = (&sm.seg[0][0])[i];
+    if constexpr (TS == 32)
+        __syncwarp();
+    else
+        __syncthreads();
 }
 
-template <typename T, int NF, int NT>
-__device__ void run_instance(Smem<T> &sm, const LaunchArgs &a) {
-    Worker<T, NF, NT> w(sm);
+template <typename T, int NF, int TS>
+__device__ void run_instance(TeamSmem<T> &sm, const Tables<T> &tab, BlockScratch &bx, const LaunchArgs &a, int tid) {
+    Worker<T, NF, TS> w(sm, tab, bx, tid);
     if (a.phases & PH_INIT_FULL) w.init_full((const double *)a.aux0 + sm.d.m_off);
     if (a.phases & PH_INIT_STATE) w.init_state((const unsigned char *)a.aux0, (const double *)a.aux1);
     for (int n = 0; n < a.nsteps; ++n) {
@@ -844,28 +931,58 @@ __device__ void run_instance(Smem<T> &sm, const LaunchArgs &a) {
     if (a.phases & PH_FINEST) w.finest((double *)a.aux0);
 }
 
+template <typename T, int TS>
+__device__ void run_team(TeamSmem<T> &sm, const Tables<T> &tab, BlockScratch &bx, const LaunchArgs &a,
+                         const InstDesc &dg, int tid) {
+    load_instance<T, TS>(sm, dg, tid);
+    switch (sm.d.nf) {
+    case 1: run_instance<T, 1, TS>(sm, tab, bx, a, tid); break;
+    case 2: run_instance<T, 2, TS>(sm, tab, bx, a, tid); break;
+    default: run_instance<T, 3, TS>(sm, tab, bx, a, tid); break;
+    }
+    store_instance<T, TS>(sm, tid);
+}
+
+// Persistent kernel.  The queue holds instances largest first; block-team
+// instances come first.  A block takes instances one at a time while they are
+// block-team instances; at the first warp-team instance it switches to warp
+// mode for good and every warp pulls instances on its own.
 template <typename T, int NT, int MINB>
 __global__ void __launch_bounds__(NT, MINB) mr_persistent(LaunchArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    Smem<T> &sm = *reinterpret_cast<Smem<T> *>(smem_raw);
-    // tables: once per block
+    BlockSmem<T, NT> &bs = *reinterpret_cast<BlockSmem<T, NT> *>(smem_raw);
     {
         const uint32_t *src = (const uint32_t *)a.tables;
-        uint32_t *dst = (uint32_t *)&sm.tab;
+        uint32_t *dst = (uint32_t *)&bs.tab;
         for (int i = threadIdx.x; i < (int)(sizeof(Tables<T>) / 4); i += NT) dst[i] = src[i];
     }
+    int idx;
     for (;;) {
-        if (threadIdx.x == 0) sm.idx = atomicAdd(a.queue, 1);
+        if (threadIdx.x == 0) bs.idx = atomicAdd(a.queue, 1);
         __syncthreads();
-        int idx = sm.idx;
-        if (idx >= a.n) break;
-        load_instance<T>(sm, a.descs[a.order[idx]]);
-        switch (sm.d.nf) {
-        case 1: run_instance<T, 1, NT>(sm, a); break;
-        case 2: run_instance<T, 2, NT>(sm, a); break;
-        default: run_instance<T, 3, NT>(sm, a); break;
-        }
-        store_instance<T>(sm);
+        idx = bs.idx;
+        __syncthreads();
+        if (idx >= a.n) return;
+        const InstDesc &dg = a.descs[a.order[idx]];
+        if (!dg.team) break;
+        run_team<T, NT>(bs.team[0], bs.tab, bs.scratch, a, dg, threadIdx.x);
+    }
+    // warp mode: warp 0 keeps idx, the other warps pull their own
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    TeamSmem<T> &sm = bs.team[warp];
+    int my = idx;
+    if (warp != 0) {
+        if (lane == 0) sm.idx = atomicAdd(a.queue, 1);
+        __syncwarp();
+        my = sm.idx;
+        __syncwarp();
+    }
+    while (my < a.n) {
+        run_team<T, 32>(sm, bs.tab, bs.scratch, a, a.descs[a.order[my]], lane);
+        if (lane == 0) sm.idx = atomicAdd(a.queue, 1);
+        __syncwarp();
+        my = sm.idx;
+        __syncwarp();
     }
 }
 
@@ -874,12 +991,22 @@ __global__ void __launch_bounds__(NT, MINB) mr_persistent(LaunchArgs a) {
 // One translation unit per (precision, block size) instantiation keeps the
 // build parallel; mr_dispatch.cu routes a launch to the right one.
 #define MRG_INSTANTIATE(T, NT, MINB, TAG)                                                          \
+    static int mrg_attr_##TAG() {                                                                 \
+        static int rc = (int)cudaFuncSetAttribute(mrg::mr_persistent<T, NT, MINB>,                \
+                                                  cudaFuncAttributeMaxDynamicSharedMemorySize,     \
+                                                  (int)sizeof(mrg::BlockSmem<T, NT>));             \
+        return rc;                                                                                \
+    }                                                                                             \
     int mrg_launch_##TAG(int grid, const mrg::LaunchArgs &a, cudaStream_t s) {                     \
-        mrg::mr_persistent<T, NT, MINB><<<grid, NT, sizeof(mrg::Smem<T>), s>>>(a);                  \
+        int rc = mrg_attr_##TAG();                                                                \
+        if (rc) return rc;                                                                        \
+        mrg::mr_persistent<T, NT, MINB><<<grid, NT, sizeof(mrg::BlockSmem<T, NT>), s>>>(a);         \
         return (int)cudaGetLastError();                                                           \
     }                                                                                             \
     int mrg_occ_##TAG(int *nb) {                                                                  \
+        int rc = mrg_attr_##TAG();                                                                \
+        if (rc) return rc;                                                                        \
         return (int)cudaOccupancyMaxActiveBlocksPerMultiprocessor(nb, mrg::mr_persistent<T, NT, MINB>, \
-                                                                   NT, sizeof(mrg::Smem<T>));       \
+                                                                   NT, sizeof(mrg::BlockSmem<T, NT>)); \
     }                                                                                             \
-    size_t mrg_smem_##TAG() { return sizeof(mrg::Smem<T>); }
+    size_t mrg_smem_##TAG() { return sizeof(mrg::BlockSmem<T, NT>); }
