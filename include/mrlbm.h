@@ -172,6 +172,15 @@ mr_status mr_set_launch(mr_ctx *ctx, int block, int grid, int block_team_jmax);
  * Host-only query, no device needed. */
 mr_status mr_reconstruction_coefficients(int dj, int kind, double *out);
 
+/* Tracing: SM clock cycles spent by instance inst in each phase of the step,
+ * accumulated since its initial state, in the order
+ *   projection (adapt), details + threshold, enlargement, grading + marking,
+ *   list compaction, data transfer, collision, projection (step), ghosts,
+ *   reconstruction, stream + audit
+ * (n >= 11 slots).  Only a library compiled with MRG_PHASE_TIMERS records
+ * them; otherwise the cycles are zero and MR_ERR_STATE is returned. */
+mr_status mr_phase_times(mr_ctx *ctx, int inst, unsigned long long *cycles, int n);
+
 /* Number of instances, and the number of kernel launches issued so far. */
 mr_status mr_info(const mr_ctx *ctx, int *n_instances, long long *launches);
 

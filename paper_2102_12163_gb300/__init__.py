@@ -192,6 +192,14 @@ class MRLBM:
         capi.check(self.h, self.lib.mr_stats(self.h, ctypes.byref(u), ctypes.byref(s), ctypes.byref(lv)))
         return u.value, s.value, lv.value
 
+    def phase_times(self, inst: int = 0):
+        """SM cycles per phase of instance inst (phase-timer build only)."""
+        arr = (ctypes.c_ulonglong * 16)()
+        rc = self.lib.mr_phase_times(self.h, inst, arr, 16)
+        if rc not in (capi.MR_OK, capi.MR_ERR_STATE):
+            capi.check(self.h, rc)
+        return dict(zip(capi.PHASES, arr[: len(capi.PHASES)]))
+
     def launches(self) -> int:
         n, l = ctypes.c_int(), ctypes.c_longlong()
         capi.check(self.h, self.lib.mr_info(self.h, ctypes.byref(n), ctypes.byref(l)))

@@ -15,6 +15,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 LIB = os.path.join(HERE, "libmrlbm.so")
+PROF_LIB = os.path.join(HERE, "libmrlbm_prof.so")  # with per-phase clock timers
 BUILD = os.path.join(HERE, "_build")
 
 NVCC = os.environ.get("NVCC", "nvcc")
@@ -31,22 +32,27 @@ def _deps() -> list[str]:
         glob.glob(os.path.join(INCLUDE, "*.h"))
 
 
-def up_to_date() -> bool:
-    if not os.path.exists(LIB):
+def up_to_date(profile: bool = False) -> bool:
+    lib = PROF_LIB if profile else LIB
+    if not os.path.exists(lib):
         return False
-    t = os.path.getmtime(LIB)
+    t = os.path.getmtime(lib)
     return all(os.path.getmtime(p) <= t for p in _deps())
 
 
-def build(force: bool = False, verbose: bool = False) -> str:
-    if not force and up_to_date():
-        return LIB
-    os.makedirs(BUILD, exist_ok=True)
+def build(force: bool = False, verbose: bool = False, profile: bool = False) -> str:
+    """Build libmrlbm.so, or with profile=True the phase-timer variant."""
+    lib = PROF_LIB if profile else LIB
+    if not force and up_to_date(profile):
+        return lib
+    bdir = BUILD + ("_prof" if profile else "")
+    os.makedirs(bdir, exist_ok=True)
     srcs = _sources()
+    extra = ["-DMRG_PHASE_TIMERS"] if profile else []
 
     def compile_one(src: str) -> str:
-        obj = os.path.join(BUILD, os.path.basename(src)[:-3] + ".o")
-        cmd = [NVCC, *ARCH, *FLAGS, "-c", src, "-o", obj]
+        obj = os.path.join(bdir, os.path.basename(src)[:-3] + ".o")
+        cmd = [NVCC, *ARCH, *FLAGS, *extra, "-c", src, "-o", obj]
         if verbose:
             cmd.insert(1, "-Xptxas=-v")
         r = subprocess.run(cmd, capture_output=True, text=True)
@@ -59,9 +65,9 @@ def build(force: bool = False, verbose: bool = False) -> str:
     workers = max(1, min(len(srcs), os.cpu_count() or 4))
     with ThreadPoolExecutor(workers) as ex:
         objs = list(ex.map(compile_one, srcs))
-    tmp = LIB + f".{os.getpid()}.tmp"
+    tmp = lib + f".{os.getpid()}.tmp"
     r = subprocess.run([NVCC, *ARCH, "-shared", "-o", tmp, *objs], capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stderr}")
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib

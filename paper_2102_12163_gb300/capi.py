@@ -52,6 +52,7 @@ SIGNATURES = {
     "mr_stats": [_vp, _P(ctypes.c_ulonglong), _P(ctypes.c_ulonglong), _P(ctypes.c_longlong)],
     "mr_set_launch": [_vp, _i, _i, _i],
     "mr_reconstruction_coefficients": [_i, _i, _P(_d)],
+    "mr_phase_times": [_vp, _i, _P(ctypes.c_ulonglong), _i],
     "mr_info": [_vp, _P(_i), _P(ctypes.c_longlong)],
     "mr_last_error": [_vp, ctypes.c_char_p, _i],
     "mr_destroy": [_vp],
@@ -60,16 +61,21 @@ SIGNATURES = {
 _lib = None
 
 
-def load(build_if_missing: bool = True) -> ctypes.CDLL:
-    """Load libmrlbm.so; raises if it cannot be built or loaded."""
+PHASES = ["projection (adapt)", "details + threshold", "enlargement", "grading + marking", "list compaction",
+          "data transfer", "collision", "projection (step)", "ghosts", "reconstruction", "stream + audit"]
+
+
+def load(build_if_missing: bool = True, profile: bool = False) -> ctypes.CDLL:
+    """Load libmrlbm.so (or the phase-timer build with profile=True); raises if
+    it cannot be built or loaded."""
     global _lib
     if _lib is not None:
         return _lib
-    path = _build.LIB
-    if not os.path.exists(path) or not _build.up_to_date():
+    path = _build.PROF_LIB if profile else _build.LIB
+    if not os.path.exists(path) or not _build.up_to_date(profile):
         if not build_if_missing:
             raise RuntimeError(f"CUDA library {path} is missing; run __graft_entry__.build()")
-        _build.build()
+        _build.build(profile=profile)
     L = ctypes.CDLL(path)
     for name, args in SIGNATURES.items():
         fn = getattr(L, name)

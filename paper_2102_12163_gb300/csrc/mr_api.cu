@@ -58,6 +58,7 @@ struct mr_ctx {
     bool bound = false, initialised = false;
     int block = 0, grid = 0, grid_req = 0, sms = 0;
     int team_jmax = -1;  // instances with Jmax >= this get a whole block (-1: default)
+    int mask_cap = 0;    // words per bitmask a block team keeps in shared memory
     long long launches = 0;
     std::string err;
 
@@ -221,6 +222,7 @@ static int launch(mr_ctx *c, int phases, int nsteps, int only_inst, const void *
     a.aux0 = aux0;
     a.aux1 = aux1;
     a.tables = c->ws + c->off_tab + (c->fp32() ? sizeof(Tables<double>) : 0);
+    a.smem_mask_words = c->mask_cap;
     int rc = c->cuda(cudaMemsetAsync(a.queue, 0, sizeof(int), c->stream), "cudaMemsetAsync");
     if (rc) return rc;
     int grid = std::min(a.n, c->grid);
@@ -372,7 +374,7 @@ mr_status mr_bind(mr_ctx *c, void *ws, size_t bytes, void *stream) {
     }
     // team per instance: a whole block from team_jmax on (a lone instance always
     // gets the block), one warp below
-    int tj = c->team_jmax >= 0 ? c->team_jmax : 13;
+    int tj = c->team_jmax >= 0 ? c->team_jmax : 0;
     for (int i = 0; i < n; ++i) dd[i].team = (n == 1 || c->desc[i].Jmax >= tj) ? 1 : 0;
     c->hdesc = dd;
     // processing order: block-team instances first, each group largest first
@@ -400,8 +402,18 @@ mr_status mr_bind(mr_ctx *c, void *ws, size_t bytes, void *stream) {
     if ((rc = c->cuda(cudaMemcpyAsync(c->ws + c->off_tab + sizeof td, &tf, sizeof tf, cudaMemcpyHostToDevice, s), "upload")))
         return (mr_status)rc;
     if ((rc = c->cuda(cudaStreamSynchronize(s), "cudaStreamSynchronize"))) return (mr_status)rc;
+    // shared-memory bitmasks for block teams: as many words as the largest
+    // block-team instance needs, within a per-block budget (a lone instance
+    // may use most of the SM; a batch keeps several blocks resident)
+    int wmax = 0;
+    for (int i = 0; i < n; ++i)
+        if (dd[i].team) wmax = std::max(wmax, dd[i].Wtot);
+    size_t budget = (n == 1 ? 220u : 48u) * 1024u, base = mrg_smem_bytes(c->fp32(), c->block, 0);
+    int fit = budget > base ? (int)((budget - base) / (NMASK * sizeof(uint32_t))) : 0;
+    c->mask_cap = std::min(wmax, fit);
     int nb = 0;
-    if ((rc = c->cuda((cudaError_t)mrg_occupancy(c->fp32(), c->block, &nb), "occupancy"))) return (mr_status)rc;
+    if ((rc = c->cuda((cudaError_t)mrg_occupancy(c->fp32(), c->block, c->mask_cap, &nb), "occupancy")))
+        return (mr_status)rc;
     c->grid = c->grid_req > 0 ? c->grid_req : std::max(1, nb) * c->sms;
     c->bound = true;
     c->initialised = false;
@@ -662,8 +674,12 @@ mr_status mr_set_launch(mr_ctx *c, int block, int grid, int block_team_jmax) {
     c->grid_req = grid;
     if (block_team_jmax >= 0) c->team_jmax = block_team_jmax;
     if (c->bound) {
+        // keep the shared-memory request of the new block size within the SM
+        size_t base = mrg_smem_bytes(c->fp32(), c->block, 0), limit = 220u * 1024u;
+        int fit = limit > base ? (int)((limit - base) / (NMASK * sizeof(uint32_t))) : 0;
+        c->mask_cap = std::min(c->mask_cap, fit);
         int nb = 0;
-        int rc = c->cuda((cudaError_t)mrg_occupancy(c->fp32(), c->block, &nb), "occupancy");
+        int rc = c->cuda((cudaError_t)mrg_occupancy(c->fp32(), c->block, c->mask_cap, &nb), "occupancy");
         if (rc) return (mr_status)rc;
         c->grid = grid > 0 ? grid : std::max(1, nb) * c->sms;
     }
@@ -683,6 +699,20 @@ mr_status mr_reconstruction_coefficients(int dj, int kind, double *out) {
     int n = kind == 2 ? 2 : 4;
     for (int j = 0; j < n; ++j) out[j] = src[j];
     return MR_OK;
+}
+
+mr_status mr_phase_times(mr_ctx *c, int inst, unsigned long long *cycles, int n) {
+    if (!c || !cycles || inst < 0 || inst >= c->n() || n < NPHASE) return MR_ERR_ARG;
+    if (!c->bound) return (mr_status)c->fail(MR_ERR_STATE, "not bound");
+    InstState st;
+    int rc = read_state(c, inst, &st);
+    if (rc) return (mr_status)rc;
+    for (int p = 0; p < NPHASE; ++p) cycles[p] = st.ptime[p];
+#ifdef MRG_PHASE_TIMERS
+    return MR_OK;
+#else
+    return (mr_status)c->fail(MR_ERR_STATE, "library built without phase timers (zeros returned)");
+#endif
 }
 
 mr_status mr_info(const mr_ctx *c, int *n, long long *launches) {

@@ -4,29 +4,29 @@
 #include "mr_common.h"
 
 int mrg_launch_f64_128(int, const mrg::LaunchArgs &, cudaStream_t);
-int mrg_occ_f64_128(int *);
-size_t mrg_smem_f64_128();
+int mrg_occ_f64_128(int, int *);
+size_t mrg_smem_f64_128(int);
 int mrg_launch_f64_256(int, const mrg::LaunchArgs &, cudaStream_t);
-int mrg_occ_f64_256(int *);
-size_t mrg_smem_f64_256();
+int mrg_occ_f64_256(int, int *);
+size_t mrg_smem_f64_256(int);
 int mrg_launch_f64_512(int, const mrg::LaunchArgs &, cudaStream_t);
-int mrg_occ_f64_512(int *);
-size_t mrg_smem_f64_512();
+int mrg_occ_f64_512(int, int *);
+size_t mrg_smem_f64_512(int);
 int mrg_launch_f64_1024(int, const mrg::LaunchArgs &, cudaStream_t);
-int mrg_occ_f64_1024(int *);
-size_t mrg_smem_f64_1024();
+int mrg_occ_f64_1024(int, int *);
+size_t mrg_smem_f64_1024(int);
 int mrg_launch_f32_128(int, const mrg::LaunchArgs &, cudaStream_t);
-int mrg_occ_f32_128(int *);
-size_t mrg_smem_f32_128();
+int mrg_occ_f32_128(int, int *);
+size_t mrg_smem_f32_128(int);
 int mrg_launch_f32_256(int, const mrg::LaunchArgs &, cudaStream_t);
-int mrg_occ_f32_256(int *);
-size_t mrg_smem_f32_256();
+int mrg_occ_f32_256(int, int *);
+size_t mrg_smem_f32_256(int);
 int mrg_launch_f32_512(int, const mrg::LaunchArgs &, cudaStream_t);
-int mrg_occ_f32_512(int *);
-size_t mrg_smem_f32_512();
+int mrg_occ_f32_512(int, int *);
+size_t mrg_smem_f32_512(int);
 int mrg_launch_f32_1024(int, const mrg::LaunchArgs &, cudaStream_t);
-int mrg_occ_f32_1024(int *);
-size_t mrg_smem_f32_1024();
+int mrg_occ_f32_1024(int, int *);
+size_t mrg_smem_f32_1024(int);
 
 int mrg_launch(bool fp32, int block, int grid, const mrg::LaunchArgs &a, void *stream) {
     cudaStream_t s = (cudaStream_t)stream;
@@ -48,23 +48,40 @@ int mrg_launch(bool fp32, int block, int grid, const mrg::LaunchArgs &a, void *s
     return (int)cudaErrorInvalidValue;
 }
 
-int mrg_occupancy(bool fp32, int block, int *nb) {
+int mrg_occupancy(bool fp32, int block, int mask_words, int *nb) {
     if (fp32) {
         switch (block) {
-        case 128: return mrg_occ_f32_128(nb);
-        case 256: return mrg_occ_f32_256(nb);
-        case 512: return mrg_occ_f32_512(nb);
-        case 1024: return mrg_occ_f32_1024(nb);
+        case 128: return mrg_occ_f32_128(mask_words, nb);
+        case 256: return mrg_occ_f32_256(mask_words, nb);
+        case 512: return mrg_occ_f32_512(mask_words, nb);
+        case 1024: return mrg_occ_f32_1024(mask_words, nb);
         }
     } else {
         switch (block) {
-        case 128: return mrg_occ_f64_128(nb);
-        case 256: return mrg_occ_f64_256(nb);
-        case 512: return mrg_occ_f64_512(nb);
-        case 1024: return mrg_occ_f64_1024(nb);
+        case 128: return mrg_occ_f64_128(mask_words, nb);
+        case 256: return mrg_occ_f64_256(mask_words, nb);
+        case 512: return mrg_occ_f64_512(mask_words, nb);
+        case 1024: return mrg_occ_f64_1024(mask_words, nb);
         }
     }
     return (int)cudaErrorInvalidValue;
 }
 
-size_t mrg_smem_bytes(bool fp32) { return fp32 ? mrg_smem_f32_256() : mrg_smem_f64_256(); }
+size_t mrg_smem_bytes(bool fp32, int block, int mask_words) {
+    if (fp32) {
+        switch (block) {
+        case 128: return mrg_smem_f32_128(mask_words);
+        case 256: return mrg_smem_f32_256(mask_words);
+        case 512: return mrg_smem_f32_512(mask_words);
+        case 1024: return mrg_smem_f32_1024(mask_words);
+        }
+    } else {
+        switch (block) {
+        case 128: return mrg_smem_f64_128(mask_words);
+        case 256: return mrg_smem_f64_256(mask_words);
+        case 512: return mrg_smem_f64_512(mask_words);
+        case 1024: return mrg_smem_f64_1024(mask_words);
+        }
+    }
+    return 0;
+}

@@ -168,6 +168,10 @@ struct TeamSmem {
     int cur, nleaf, status, near_ties;
     int idx;
     int g0s, gbase;  // level_of_word constants
+#ifdef MRG_PHASE_TIMERS
+    long long tlast;
+    unsigned long long ptime[NPHASE];
+#endif
 };
 
 // block-team scratch (scan partials and reduction slots of the warps)
@@ -282,11 +286,11 @@ struct Worker {
     uint32_t *M;  // mask base
     int tid;      // rank in the team
 
-    __device__ Worker(TeamSmem<T> &s, const Tables<T> &tb, BlockScratch &x, int rank)
+    __device__ Worker(TeamSmem<T> &s, const Tables<T> &tb, BlockScratch &x, int rank, uint32_t *masks)
         : sm(s), tab(tb), bx(x), d(s.d), tid(rank) {
         V = (T *)d.V;
         Phi = (T *)d.Phi;
-        M = d.masks;
+        M = masks;
     }
 
     __device__ __forceinline__ void sync() const {
@@ -294,6 +298,20 @@ struct Worker {
             __syncwarp();
         else
             __syncthreads();
+    }
+
+    // profiling build: cycles since the previous tick charged to phase p (after a team barrier)
+    __device__ __forceinline__ void tick(int p) {
+#ifdef MRG_PHASE_TIMERS
+        sync();
+        if (tid == 0) {
+            long long t = clock64();
+            if (p < NPHASE) sm.ptime[p] += (unsigned long long)(t - sm.tlast);
+            sm.tlast = t;
+        }
+#else
+        (void)p;
+#endif
     }
 
     __device__ __forceinline__ uint32_t *mask(int m) { return M + (long long)m * d.Wtot; }
@@ -574,15 +592,22 @@ struct Worker {
     // ---- mesh adaptation ----------------------------------------------------
     __device__ void adapt() {
         uint32_t *Ro = mask(sm.cur), *Rn = mask(sm.cur ^ 1);
+        tick(NPHASE);
         upsweep();
         sync();
+        tick(T_UPSWEEP_A);
         details();
         sync();
+        tick(T_DETAILS);
         enlarge(Rn);
         sync();
+        tick(T_ENLARGE);
         grade_and_mark(Rn, Ro, true);
+        tick(T_GRADE);
         build_lists(Rn);
+        tick(T_LISTS);
         predict_fill(L_PRED);
+        tick(T_TRANSFER);
         if (tid == 0) {
             sm.cur ^= 1;
             sm.updates += (unsigned long long)sm.nleaf;
@@ -594,6 +619,7 @@ struct Worker {
     __device__ void lbm_step() {
         const uint32_t *leaves = list(L_LEAF);
         int nl = sm.nleaf;
+        tick(NPHASE);
         // S1 leaves collision
         for (int i = tid; i < nl; i += TS) {
             uint32_t ent = leaves[i];
@@ -607,11 +633,16 @@ struct Worker {
             for (int h = 0; h < Q; ++h) row(h, l)[k] = f[h];
         }
         sync();
+        tick(T_COLLIDE);
         upsweep();             // S2
+        tick(T_UPSWEEP_S);
         predict_fill(L_GH);    // S3
+        tick(T_GHOSTS);
         reconstruct_edges();   // S4
         sync();
+        tick(T_RECON);
         stream_and_audit();    // S5
+        tick(T_STREAM);
     }
 
     // S4: first / last finest-cell values of every leaf -> Phi
@@ -872,6 +903,10 @@ __device__ void load_instance(TeamSmem<T> &sm, const InstDesc &dg, int tid) {
         sm.steps = st.steps;
         sm.audit = st.audit;
         for (int j = 0; j < 3; ++j) sm.mass[j] = st.mass[j];
+#ifdef MRG_PHASE_TIMERS
+        for (int p = 0; p < NPHASE; ++p) sm.ptime[p] = st.ptime[p];
+        sm.tlast = clock64();
+#endif
         int Jmin = dg.Jmin, Jmax = dg.Jmax;
         int o = 0;
         for (int l = Jmin; l <= Jmax; ++l) {
@@ -911,6 +946,9 @@ __device__ void store_instance(TeamSmem<T> &sm, int tid) {
         st.steps = sm.steps;
         st.audit = sm.audit;
         for (int j = 0; j < 3; ++j) st.mass[j] = sm.mass[j];
+#ifdef MRG_PHASE_TIMERS
+        for (int p = 0; p < NPHASE; ++p) st.ptime[p] = sm.ptime[p];
+#endif
     }
     for (int i = tid; i < NLIST * (MAXLEV + 2); i += TS) (&st.seg[0][0])[i] = (&sm.seg[0][0])[i];
     if constexpr (TS == 32)
@@ -920,8 +958,9 @@ __device__ void store_instance(TeamSmem<T> &sm, int tid) {
 }
 
 template <typename T, int NF, int TS>
-__device__ void run_instance(TeamSmem<T> &sm, const Tables<T> &tab, BlockScratch &bx, const LaunchArgs &a, int tid) {
-    Worker<T, NF, TS> w(sm, tab, bx, tid);
+__device__ void run_instance(TeamSmem<T> &sm, const Tables<T> &tab, BlockScratch &bx, const LaunchArgs &a, int tid,
+                             uint32_t *masks) {
+    Worker<T, NF, TS> w(sm, tab, bx, tid, masks);
     if (a.phases & PH_INIT_FULL) w.init_full((const double *)a.aux0 + sm.d.m_off);
     if (a.phases & PH_INIT_STATE) w.init_state((const unsigned char *)a.aux0, (const double *)a.aux1);
     for (int n = 0; n < a.nsteps; ++n) {
@@ -931,14 +970,38 @@ __device__ void run_instance(TeamSmem<T> &sm, const Tables<T> &tab, BlockScratch
     if (a.phases & PH_FINEST) w.finest((double *)a.aux0);
 }
 
+// Bitmasks live in shared memory (smask, room for `cap` words per mask) when the
+// instance fits: the current tree is copied in at the start and back at the
+// end, KEEP / REF start cleared, the other masks are rebuilt by every step.
 template <typename T, int TS>
 __device__ void run_team(TeamSmem<T> &sm, const Tables<T> &tab, BlockScratch &bx, const LaunchArgs &a,
-                         const InstDesc &dg, int tid) {
+                         const InstDesc &dg, int tid, uint32_t *smask, int cap) {
     load_instance<T, TS>(sm, dg, tid);
+    const int W = sm.d.Wtot;
+    const bool local = smask != nullptr && W <= cap;
+    uint32_t *masks = local ? smask : sm.d.masks;
+    if (local) {
+        const uint32_t *gr = sm.d.masks + (long long)sm.cur * W;
+        uint32_t *lr = smask + sm.cur * W;
+        for (int g = tid; g < W; g += TS) {
+            lr[g] = gr[g];
+            smask[M_KEEP * W + g] = 0u;
+            smask[M_REF * W + g] = 0u;
+        }
+        if constexpr (TS == 32)
+            __syncwarp();
+        else
+            __syncthreads();
+    }
     switch (sm.d.nf) {
-    case 1: run_instance<T, 1, TS>(sm, tab, bx, a, tid); break;
-    case 2: run_instance<T, 2, TS>(sm, tab, bx, a, tid); break;
-    default: run_instance<T, 3, TS>(sm, tab, bx, a, tid); break;
+    case 1: run_instance<T, 1, TS>(sm, tab, bx, a, tid, masks); break;
+    case 2: run_instance<T, 2, TS>(sm, tab, bx, a, tid, masks); break;
+    default: run_instance<T, 3, TS>(sm, tab, bx, a, tid, masks); break;
+    }
+    if (local) {
+        uint32_t *gr = sm.d.masks + (long long)sm.cur * W;
+        const uint32_t *lr = smask + sm.cur * W;
+        for (int g = tid; g < W; g += TS) gr[g] = lr[g];
     }
     store_instance<T, TS>(sm, tid);
 }
@@ -951,6 +1014,9 @@ template <typename T, int NT, int MINB>
 __global__ void __launch_bounds__(NT, MINB) mr_persistent(LaunchArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     BlockSmem<T, NT> &bs = *reinterpret_cast<BlockSmem<T, NT> *>(smem_raw);
+    uint32_t *smask = a.smem_mask_words > 0
+                          ? reinterpret_cast<uint32_t *>(smem_raw + ((sizeof(BlockSmem<T, NT>) + 15) / 16) * 16)
+                          : nullptr;
     {
         const uint32_t *src = (const uint32_t *)a.tables;
         uint32_t *dst = (uint32_t *)&bs.tab;
@@ -965,7 +1031,7 @@ __global__ void __launch_bounds__(NT, MINB) mr_persistent(LaunchArgs a) {
         if (idx >= a.n) return;
         const InstDesc &dg = a.descs[a.order[idx]];
         if (!dg.team) break;
-        run_team<T, NT>(bs.team[0], bs.tab, bs.scratch, a, dg, threadIdx.x);
+        run_team<T, NT>(bs.team[0], bs.tab, bs.scratch, a, dg, threadIdx.x, smask, a.smem_mask_words);
     }
     // warp mode: warp 0 keeps idx, the other warps pull their own
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -978,7 +1044,7 @@ __global__ void __launch_bounds__(NT, MINB) mr_persistent(LaunchArgs a) {
         __syncwarp();
     }
     while (my < a.n) {
-        run_team<T, 32>(sm, bs.tab, bs.scratch, a, a.descs[a.order[my]], lane);
+        run_team<T, 32>(sm, bs.tab, bs.scratch, a, a.descs[a.order[my]], lane, nullptr, 0);
         if (lane == 0) sm.idx = atomicAdd(a.queue, 1);
         __syncwarp();
         my = sm.idx;
@@ -991,22 +1057,26 @@ __global__ void __launch_bounds__(NT, MINB) mr_persistent(LaunchArgs a) {
 // One translation unit per (precision, block size) instantiation keeps the
 // build parallel; mr_dispatch.cu routes a launch to the right one.
 #define MRG_INSTANTIATE(T, NT, MINB, TAG)                                                          \
+    static size_t mrg_dyn_##TAG(int mask_words) {                                                 \
+        size_t base = (sizeof(mrg::BlockSmem<T, NT>) + 15) / 16 * 16;                              \
+        return base + (size_t)mask_words * mrg::NMASK * sizeof(uint32_t);                          \
+    }                                                                                             \
     static int mrg_attr_##TAG() {                                                                 \
         static int rc = (int)cudaFuncSetAttribute(mrg::mr_persistent<T, NT, MINB>,                \
                                                   cudaFuncAttributeMaxDynamicSharedMemorySize,     \
-                                                  (int)sizeof(mrg::BlockSmem<T, NT>));             \
+                                                  227 * 1024);                                     \
         return rc;                                                                                \
     }                                                                                             \
     int mrg_launch_##TAG(int grid, const mrg::LaunchArgs &a, cudaStream_t s) {                     \
         int rc = mrg_attr_##TAG();                                                                \
         if (rc) return rc;                                                                        \
-        mrg::mr_persistent<T, NT, MINB><<<grid, NT, sizeof(mrg::BlockSmem<T, NT>), s>>>(a);         \
+        mrg::mr_persistent<T, NT, MINB><<<grid, NT, mrg_dyn_##TAG(a.smem_mask_words), s>>>(a);      \
         return (int)cudaGetLastError();                                                           \
     }                                                                                             \
-    int mrg_occ_##TAG(int *nb) {                                                                  \
+    int mrg_occ_##TAG(int mask_words, int *nb) {                                                  \
         int rc = mrg_attr_##TAG();                                                                \
         if (rc) return rc;                                                                        \
         return (int)cudaOccupancyMaxActiveBlocksPerMultiprocessor(nb, mrg::mr_persistent<T, NT, MINB>, \
-                                                                   NT, sizeof(mrg::BlockSmem<T, NT>)); \
+                                                                   NT, mrg_dyn_##TAG(mask_words)); \
     }                                                                                             \
-    size_t mrg_smem_##TAG() { return sizeof(mrg::BlockSmem<T, NT>); }
+    size_t mrg_smem_##TAG(int mask_words) { return mrg_dyn_##TAG(mask_words); }
