@@ -189,6 +189,39 @@ mr_status mr_last_error(const mr_ctx *ctx, char *buf, int len);
 
 mr_status mr_destroy(mr_ctx *ctx);
 
+/* ---- running without any device allocation ----------------------------- */
+
+/* Size of the scratch area built into the library for mr_run_static. */
+#define MR_STATIC_SCRATCH_BYTES (16u << 20)
+
+/* The paper has no counterpart to this call; it is here for callers that
+ * cannot allocate device memory when they need to run a problem: a host
+ * program that forbids new device allocations after start-up, a plug-in whose
+ * host application owns every device buffer, or code that must not risk the
+ * blocking and device-wide synchronisation an allocation can cause.
+ *
+ * mr_run_static runs one instance (desc, precision) from its initial datum
+ * for nsteps adaptive steps and writes the conserved moments reconstructed on
+ * every finest cell, exactly as mr_set_initial + mr_advance + mr_get_finest
+ * of a context would.  It allocates nothing: no cudaMalloc, no cudaFree, no
+ * allocating library routine.  Its working memory is a fixed area of
+ * MR_STATIC_SCRATCH_BYTES that is part of the library's device image, held
+ * by every GPU that loads the library until the process exits.
+ *   m_cons    device-readable input, n * 2^Jmax doubles (layout of mr_set_initial)
+ *   m_finest  device-writable output, n * 2^Jmax doubles (layout of mr_get_finest)
+ *   updates   optional host output: leaf-cell updates over the run; when it is
+ *             given the call waits for the stream and reports non-finite values
+ *   stream    CUDA stream the work is ordered on (NULL: legacy default stream)
+ * The first call on a device looks up the scratch area's device address (with
+ * that device current) and keeps it; make that first call before any stream
+ * capture.  An instance whose layout exceeds the area is rejected with
+ * MR_ERR_CAPACITY (FP64 Euler fits up to Jmax = 16); the message is available
+ * from mr_last_error(NULL, ...).  Every call uses the same area and leaves its
+ * contents behind; each call re-initialises what it reads, but calls whose
+ * work overlaps on the GPU (other streams, other host threads) race on it. */
+mr_status mr_run_static(const mr_instance_desc *desc, int precision, const double *m_cons, int nsteps,
+                        double *m_finest, unsigned long long *updates, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -56,6 +56,7 @@ SIGNATURES = {
     "mr_info": [_vp, _P(_i), _P(ctypes.c_longlong)],
     "mr_last_error": [_vp, ctypes.c_char_p, _i],
     "mr_destroy": [_vp],
+    "mr_run_static": [_P(mr_instance_desc), _i, _vp, _i, _vp, _P(ctypes.c_ulonglong), _vp],
 }
 
 _lib = None

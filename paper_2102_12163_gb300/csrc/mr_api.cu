@@ -735,3 +735,9 @@ mr_status mr_destroy(mr_ctx *c) {
 }
 
 }  // extern "C"
+
+// Reconstruction tables for other translation units of the library.
+void mrg_tables(Tables<double> *td, Tables<float> *tf) { make_tables(*td, *tf); }
+
+// Message reported by mr_last_error(NULL, ...) for calls without a context.
+void mrg_set_error(const char *msg) { g_create_error = msg ? msg : ""; }
