@@ -136,7 +136,7 @@ def make_workload(name: str, rank: int, n_batch: int = 4096):
         insts = W.batch(n=n_batch, seed=12163 + rank)
         desc = f"batch of {n_batch} mixed D1Q2 advection/Burgers, D1Q2^2 shallow water, D1Q2^3 Euler; Jmax 8..14; eps 1e-5..1e-2"
     else:
-        insts = [W.CONFIGS[name]()]
+        insts = [W.WORKLOADS[name]()]
         i = insts[0]
         desc = f"{name} single instance, Jmin {i.Jmin} Jmax {i.Jmax} eps {i.eps:g}"
     return insts, desc

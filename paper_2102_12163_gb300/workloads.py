@@ -217,7 +217,7 @@ def random_smooth(Jmax: int, eq: int, seed: int, Jmin: int = 2, eps: float = 1e-
     return inst
 
 
-CONFIGS = {
+WORKLOADS = {
     "advection": advection,
     "burgers": burgers,
     "shallow": shallow_water,
