@@ -155,13 +155,10 @@ mr_status mr_get_summary(mr_ctx *ctx, double *mass, int *nleaf);
 mr_status mr_stats(mr_ctx *ctx, unsigned long long *updates, unsigned long long *steps,
                    long long *leaves);
 
-/* Launch shape: threads per block (128, 256, 512 or 1024), blocks (0 = one
- * wave of resident blocks) and the team size: instances with Jmax >=
- * block_team_jmax are advanced by a whole block, smaller ones by one warp each
- * (-1 keeps the current choice; a context with one instance always uses a
- * block).  Block and grid take effect at the next launch; the team threshold
- * must be set before mr_bind. */
-mr_status mr_set_launch(mr_ctx *ctx, int block, int grid, int block_team_jmax);
+/* Launch shape: threads per block (128, 256, 512 or 1024; one block advances
+ * one instance at a time) and blocks (0 = one wave of resident blocks).
+ * Takes effect at the next launch. */
+mr_status mr_set_launch(mr_ctx *ctx, int block, int grid);
 
 /* Reconstruction coefficients used by the stream (Section 3.3 with gamma = 1):
  * for a leaf at level gap dj = Jmax - l (0 <= dj <= 24), kind 0 gives the

@@ -40,7 +40,7 @@ class MRLBM:
     """
 
     def __init__(self, instances, precision: int = MR_FP64, device: str = "cuda:0", block: int | None = None,
-                 stream=None, block_team_jmax: int | None = None):
+                 stream=None):
         import torch
 
         self.lib = capi.load()
@@ -67,9 +67,8 @@ class MRLBM:
             self.stream = stream if stream is not None else torch.cuda.Stream(self.device)
             # caller-owned workspace (torch allocations are 512-byte aligned)
             self.ws = torch.empty(self.workspace_bytes, dtype=torch.uint8, device=self.device)
-        if block is not None or block_team_jmax is not None:
-            self.set_launch(block or (256 if len(self.instances) > 1 else 1024), 0,
-                            -1 if block_team_jmax is None else block_team_jmax)
+        if block is not None:
+            self.set_launch(block, 0)
         capi.check(self.h, self.lib.mr_bind(self.h, ctypes.c_void_p(self.ws.data_ptr()), self.workspace_bytes,
                                             ctypes.c_void_p(self.stream.cuda_stream)))
 
@@ -85,10 +84,9 @@ class MRLBM:
         except Exception:
             pass
 
-    def set_launch(self, block: int, grid: int = 0, block_team_jmax: int = -1):
-        """Threads per block (128, 256, 512 or 1024), blocks (0: one resident
-        wave) and the Jmax from which an instance gets a whole block."""
-        capi.check(self.h, self.lib.mr_set_launch(self.h, block, grid, block_team_jmax))
+    def set_launch(self, block: int, grid: int = 0):
+        """Threads per block (128, 256, 512 or 1024) and blocks (0: one resident wave)."""
+        capi.check(self.h, self.lib.mr_set_launch(self.h, block, grid))
 
     # -- state -------------------------------------------------------------
     def initial_data(self) -> np.ndarray:

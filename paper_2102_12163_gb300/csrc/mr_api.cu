@@ -57,7 +57,6 @@ struct mr_ctx {
     cudaStream_t stream = nullptr;
     bool bound = false, initialised = false;
     int block = 0, grid = 0, grid_req = 0, sms = 0;
-    int team_jmax = -1;  // instances with Jmax >= this get a whole block (-1: default)
     int mask_cap = 0;    // words per bitmask a block team keeps in shared memory
     long long launches = 0;
     std::string err;
@@ -146,7 +145,6 @@ static void layout(mr_ctx *c) {
         h.S = S;
         h.N = N;
         h.m_off = c->m_off[i];
-        h.team = 1;
         c->inst_off[i] = o;
         size_t vb = c->vbytes();
         size_t oV = 0, oPhi = align_up(oV + vb * q * S), oM = align_up(oPhi + vb * q * (N + 1));
@@ -372,17 +370,11 @@ mr_status mr_bind(mr_ctx *c, void *ws, size_t bytes, void *stream) {
         for (auto &d : c->desc) jmax = std::max(jmax, d.Jmax);
         c->block = n == 1 ? (jmax >= 12 ? 1024 : 512) : 256;
     }
-    // team per instance: a whole block from team_jmax on (a lone instance always
-    // gets the block), one warp below
-    int tj = c->team_jmax >= 0 ? c->team_jmax : 0;
-    for (int i = 0; i < n; ++i) dd[i].team = (n == 1 || c->desc[i].Jmax >= tj) ? 1 : 0;
     c->hdesc = dd;
-    // processing order: block-team instances first, each group largest first
-    // (nf 2^Jmax as the cost estimate); the kernel relies on the grouping
+    // processing order: largest instances first (nf 2^Jmax as the cost estimate)
     std::vector<int> order(n), ident(n);
     for (int i = 0; i < n; ++i) order[i] = ident[i] = i;
     std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
-        if (dd[x].team != dd[y].team) return dd[x].team > dd[y].team;
         double cx = (double)dd[x].nf * std::ldexp(1.0, dd[x].Jmax);
         double cy = (double)dd[y].nf * std::ldexp(1.0, dd[y].Jmax);
         return cx > cy;
@@ -402,13 +394,15 @@ mr_status mr_bind(mr_ctx *c, void *ws, size_t bytes, void *stream) {
     if ((rc = c->cuda(cudaMemcpyAsync(c->ws + c->off_tab + sizeof td, &tf, sizeof tf, cudaMemcpyHostToDevice, s), "upload")))
         return (mr_status)rc;
     if ((rc = c->cuda(cudaStreamSynchronize(s), "cudaStreamSynchronize"))) return (mr_status)rc;
-    // shared-memory bitmasks for block teams: as many words as the largest
-    // block-team instance needs, within a per-block budget (a lone instance
-    // may use most of the SM; a batch keeps several blocks resident)
+    // shared-memory bitmasks: as many words as the largest instance needs,
+    // within a per-block budget (a lone instance may use most of the SM; a
+    // batch keeps several blocks resident)
     int wmax = 0;
-    for (int i = 0; i < n; ++i)
-        if (dd[i].team) wmax = std::max(wmax, dd[i].Wtot);
-    size_t budget = (n == 1 ? 220u : 48u) * 1024u, base = mrg_smem_bytes(c->fp32(), c->block, 0);
+    for (int i = 0; i < n; ++i) wmax = std::max(wmax, dd[i].Wtot);
+    // resident blocks the registers allow (64 per thread) share the SM's 227 KB
+    int by_regs = std::max(1, 65536 / (c->block * 64));
+    size_t budget = n == 1 ? 220u * 1024u : (227u * 1024u) / (size_t)by_regs - 1024u;
+    size_t base = mrg_smem_bytes(c->fp32(), c->block, 0);
     int fit = budget > base ? (int)((budget - base) / (NMASK * sizeof(uint32_t))) : 0;
     c->mask_cap = std::min(wmax, fit);
     int nb = 0;
@@ -663,19 +657,18 @@ mr_status mr_stats(mr_ctx *c, unsigned long long *updates, unsigned long long *s
     return MR_OK;
 }
 
-mr_status mr_set_launch(mr_ctx *c, int block, int grid, int block_team_jmax) {
+mr_status mr_set_launch(mr_ctx *c, int block, int grid) {
     if (!c) return MR_ERR_ARG;
     if (block != 128 && block != 256 && block != 512 && block != 1024)
         return (mr_status)c->fail(MR_ERR_ARG, "block must be 128, 256, 512 or 1024");
     if (grid < 0) return (mr_status)c->fail(MR_ERR_ARG, "grid must be >= 0");
-    if (c->bound && block_team_jmax != c->team_jmax && block_team_jmax >= 0)
-        return (mr_status)c->fail(MR_ERR_STATE, "team threshold must be set before mr_bind");
     c->block = block;
     c->grid_req = grid;
-    if (block_team_jmax >= 0) c->team_jmax = block_team_jmax;
     if (c->bound) {
-        // keep the shared-memory request of the new block size within the SM
-        size_t base = mrg_smem_bytes(c->fp32(), c->block, 0), limit = 220u * 1024u;
+        // keep the shared-memory request of the new block size within its share of the SM
+        int by_regs = std::max(1, 65536 / (c->block * 64));
+        size_t base = mrg_smem_bytes(c->fp32(), c->block, 0);
+        size_t limit = c->n() == 1 ? 220u * 1024u : (227u * 1024u) / (size_t)by_regs - 1024u;
         int fit = limit > base ? (int)((limit - base) / (NMASK * sizeof(uint32_t))) : 0;
         c->mask_cap = std::min(c->mask_cap, fit);
         int nb = 0;

@@ -1,12 +1,9 @@
 // mr_kernels.cuh -- sm_103a kernels of the multiresolution-adaptive lattice
 // Boltzmann step (Bellotti, Gouarin, Graille, Massot, arXiv 2102.12163).
 //
-// A "team" owns one instance at a time and runs every phase of the step on it:
-// either a whole thread block (large instances; block barriers between phases)
-// or a single warp (small instances; warp barriers only, eight instances in
-// flight per block).  Blocks pull instances from an atomic work queue sorted
-// largest first; a block that meets a warp-team instance switches to warp mode
-// and its warps pull the rest of the queue independently.  Inside a step:
+// A thread block owns one instance at a time and runs every phase of the step
+// on it, with block barriers between phases; blocks pull instances from an
+// atomic work queue sorted largest first (persistent launch).  Inside a step:
 //
 //   adapt (Section 4.1)
 //     A1  projection up the current tree (Def. Projection operator)
@@ -151,6 +148,20 @@ __device__ __forceinline__ uint32_t dilate(Get get, int l, int wi, int r, int bc
     return out;
 }
 
+// word j of a level of W words under the boundary rule: wrapped (periodic) or
+// empty beyond the domain (copy)
+__device__ __forceinline__ uint32_t word_bc(const uint32_t *a, int j, int W, int bc) {
+    if (j < 0) return bc == 0 ? a[j + W] : 0u;
+    if (j >= W) return bc == 0 ? a[j - W] : 0u;
+    return a[j];
+}
+// 4 child bits -> 2 parent bits
+__device__ __forceinline__ uint32_t fold_low2(uint32_t x) { return ((x | (x >> 1)) & 1u) | (((x >> 2) | (x >> 3)) & 1u) << 1; }
+// dilation by one cell of a word, given the neighbouring cells just outside it
+__device__ __forceinline__ uint32_t dilate1_edges(uint32_t x, bool left, bool right) {
+    return x | (x << 1) | (x >> 1) | (left ? 1u : 0u) | (right ? 0x80000000u : 0u);
+}
+
 // ---------------------------------------------------------------------------
 // shared memory: per-team state and per-block tables
 
@@ -184,7 +195,7 @@ template <typename T, int NT>
 struct BlockSmem {
     Tables<T> tab;
     BlockScratch scratch;
-    TeamSmem<T> team[NT / 32];
+    TeamSmem<T> team;
     int idx;
 };
 
@@ -273,17 +284,19 @@ __device__ __forceinline__ T predict(const T *row, long long p, int odd, int lp,
 // ---------------------------------------------------------------------------
 // the instance worker; TS threads (a warp or the whole block) form the team
 
+constexpr int QMAX = 6;  // populations of the largest scheme (vectorial D1Q2^3)
+
 template <typename T, int NF, int TS>
 struct Worker {
-    static constexpr int Q = 2 * NF;
     static constexpr bool WARP = TS == 32;
+    static constexpr int nf = NF, q = 2 * NF;  // fields and populations of the scheme
     TeamSmem<T> &sm;
     const Tables<T> &tab;
     BlockScratch &bx;
     const InstDesc &d;
     T *V;
     T *Phi;
-    uint32_t *M;  // mask base
+    uint32_t *M;  // mask base (shared memory when the masks fit, else global)
     int tid;      // rank in the team
 
     __device__ Worker(TeamSmem<T> &s, const Tables<T> &tb, BlockScratch &x, int rank, uint32_t *masks)
@@ -292,6 +305,9 @@ struct Worker {
         Phi = (T *)d.Phi;
         M = masks;
     }
+
+    // leaves collision of the q populations of one cell
+    __device__ __forceinline__ void collide_cell(T *f) const { collide<T, NF>(d, f); }
 
     __device__ __forceinline__ void sync() const {
         if constexpr (WARP)
@@ -333,25 +349,50 @@ struct Worker {
         }
     }
 
-    // ---- A1 / S2: projection up the tree over the internal cells ----------
-    __device__ void upsweep() {
-        const uint32_t *lst = list(L_INT);
-        for (int l = d.Jmax - 1; l >= d.Jmin; --l) {
-            int b = sm.seg[L_INT][l], e = sm.seg[L_INT][l + 1];
-            if (b == e) continue;
-            for (int i = b + tid; i < e; i += TS) {
-                long long k = lst[i] & KMASK;
+    // ---- projection of the internal cells of level l (Def. Projection operator)
+    __device__ __forceinline__ void project_level(const uint32_t *lst, int l) {
+        int b = sm.seg[L_INT][l], e = sm.seg[L_INT][l + 1];
+        for (int i = b + tid; i < e; i += TS) {
+            long long k = lst[i] & KMASK;
+            typename V2<T>::type c[QMAX];
 #pragma unroll
-                for (int h = 0; h < Q; ++h) {
-                    typename V2<T>::type c = *reinterpret_cast<const typename V2<T>::type *>(row(h, l + 1) + 2 * k);
-                    row(h, l)[k] = T(0.5) * (c.x + c.y);
-                }
-            }
+            for (int h = 0; h < QMAX; ++h)
+                if (h < q) c[h] = *reinterpret_cast<const typename V2<T>::type *>(row(h, l + 1) + 2 * k);
+#pragma unroll
+            for (int h = 0; h < QMAX; ++h)
+                if (h < q) row(h, l)[k] = T(0.5) * (c[h].x + c[h].y);
+        }
+    }
+
+    // ---- S1: leaves collision (eq. LeavesCollision) ---------------------------
+    __device__ void collide_all() {
+        const uint32_t *lst = list(L_LEAF);
+        for (int i = tid; i < sm.nleaf; i += TS) {
+            uint32_t ent = lst[i];
+            int l = ent >> KBITS;
+            long long k = ent & KMASK;
+            T f[QMAX];
+#pragma unroll
+            for (int h = 0; h < QMAX; ++h)
+                if (h < q) f[h] = row(h, l)[k];
+            collide_cell(f);
+#pragma unroll
+            for (int h = 0; h < QMAX; ++h)
+                if (h < q) row(h, l)[k] = f[h];
+        }
+    }
+
+    // ---- A1 / S2: projection sweep, fine to coarse ---------------------------
+    __device__ void upsweep() {
+        const uint32_t *li = list(L_INT);
+        for (int l = d.Jmax - 1; l >= d.Jmin; --l) {
+            if (sm.seg[L_INT][l] == sm.seg[L_INT][l + 1]) continue;
+            project_level(li, l);
             sync();
         }
     }
 
-    // ---- A2: details, threshold T, Harten flags ----------------------------
+    // ---- A2: details of the pairs of the tree, threshold T, Harten flags ----
     // FP64: the detail of Section 3.2 in double.  FP32: the detail in float with
     // a rigorous bound on its rounding error; only when a threshold lies within
     // that bound is the detail recomputed in FP64 from the stored values, so
@@ -363,18 +404,19 @@ struct Worker {
         for (int i = b + tid; i < e; i += TS) {
             uint32_t ent = lst[i];
             int l = ent >> KBITS;
+            const bool hasref = l < d.Jmax;
             long long k = ent & KMASK, p = k >> 1;
             long long pl = wrapc(p - 1, l - 1, d.bc), pr = wrapc(p + 1, l - 1, d.bc);
             bool keepit, refit, tie = false;
-            const bool hasref = l < d.Jmax;
             if constexpr (sizeof(T) == 8) {
                 double D = 0.0;
 #pragma unroll
-                for (int h = 0; h < Q; ++h) {
-                    const T *rc = row(h, l - 1);
-                    double dv = row(h, l)[k] - (rc[p] + C1 * (rc[pr] - rc[pl]));
-                    D = fmax(D, fabs(dv));
-                }
+                for (int h = 0; h < QMAX; ++h)
+                    if (h < q) {
+                        const T *rc = row(h, l - 1);
+                        double dv = row(h, l)[k] - (rc[p] + C1 * (rc[pr] - rc[pl]));
+                        D = fmax(D, fabs(dv));
+                    }
                 double el = sm.eps_l[l], bl = sm.big_l[l];
                 keepit = D >= el;
                 refit = hasref && D >= bl;
@@ -382,20 +424,21 @@ struct Worker {
             } else {
                 float D = 0.0f, B = 0.0f;
 #pragma unroll
-                for (int h = 0; h < Q; ++h) {
-                    const T *rc = row(h, l - 1);
-                    float vk = row(h, l)[k], vl = rc[pl], vp = rc[p], vr = rc[pr];
-                    float dv = vk - (vp + float(C1) * (vr - vl));
-                    D = fmaxf(D, fabsf(dv));
-                    B = fmaxf(B, fabsf(vk) + fabsf(vp) + fabsf(vl) + fabsf(vr));
-                }
+                for (int h = 0; h < QMAX; ++h)
+                    if (h < q) {
+                        const T *rc = row(h, l - 1);
+                        float vk = row(h, l)[k], vl = rc[pl], vp = rc[p], vr = rc[pr];
+                        float dv = vk - (vp + float(C1) * (vr - vl));
+                        D = fmaxf(D, fabsf(dv));
+                        B = fmaxf(B, fabsf(vk) + fabsf(vp) + fabsf(vl) + fabsf(vr));
+                    }
                 B *= 0x1p-21f;  // 4 times the rounding bound of the detail evaluation
                 float el = sm.eps_f[l], bl = sm.big_f[l];
                 // the band also covers the rounding of the thresholds to float
                 bool amb = fabsf(D - el) <= B + el * 0x1p-22f || (hasref && fabsf(D - bl) <= B + bl * 0x1p-22f);
                 if (amb) {
                     double Dd = 0.0;
-                    for (int h = 0; h < Q; ++h) {
+                    for (int h = 0; h < q; ++h) {
                         const T *rc = row(h, l - 1);
                         double dv = (double)row(h, l)[k] - ((double)rc[p] + C1 * ((double)rc[pr] - (double)rc[pl]));
                         Dd = fmax(Dd, fabs(dv));
@@ -439,43 +482,92 @@ struct Worker {
     }
 
     // ---- A4: grading sweep + leaf / transfer / ghost marking -----------------
+    // Fine to coarse: the cells of level l require (l-1, floor(k/2) + delta),
+    // |delta| <= gamma = 1, with siblings (Def. Graded tree); once level l is
+    // final its leaves (no child in the tree), its transfer marks (new leaves
+    // outside the old tree and the parent stencils of finer marks) and its ghost
+    // marks (reconstruction windows k-2..k+2 of its leaves and the parent
+    // stencils of finer ghosts, outside the tree) are written.  Levels of 64
+    // cells or more work on whole words, with the neighbouring words' edge bits;
+    // the smaller levels are done by one thread without barriers.
     // grade = false only re-derives the marks of a tree known to be graded.
     __device__ void grade_and_mark(uint32_t *Rn, const uint32_t *Ro, bool grade) {
         uint32_t *LF = mask(M_LEAF), *PR = mask(M_PRED), *GH = mask(M_GH);
-        uint32_t *keep = mask(M_KEEP), *ref = mask(M_REF);
-        for (int l = d.Jmax; l >= d.Jmin; --l) {
+        const int lbig = d.Jmin > 6 ? d.Jmin : 6;
+        for (int l = d.Jmax; l >= lbig; --l) {
+            const int Wl = 1 << (l - 5);
             const uint32_t *rl = Rn + sm.woff[l];
-            const uint32_t *rf = l < d.Jmax ? Rn + sm.woff[l + 1] : nullptr;
             if (grade && l > d.Jmin + 1) {
-                // (l-1, floor(k/2) + delta), |delta| <= gamma, with siblings
                 uint32_t *rp = Rn + sm.woff[l - 1];
-                int Wp = nwords(l - 1);
-                uint32_t vb = valid_bits(l - 1);
-                for (int wp = tid; wp < Wp; wp += TS)
-                    rp[wp] |= pairexpand(dilate([&](int j) { return fold_at(rl, l, j); }, l - 1, wp, 1, d.bc)) & vb;
-            }
-            int W = nwords(l);
-            uint32_t vb = valid_bits(l);
-            const uint32_t *pf = l < d.Jmax ? PR + sm.woff[l + 1] : nullptr;
-            const uint32_t *gf = l < d.Jmax ? GH + sm.woff[l + 1] : nullptr;
-            auto leafw = [&](int j) { return rf ? (rl[j] & ~fold_at(rf, l + 1, j)) : rl[j]; };
-            for (int wi = tid; wi < W; wi += TS) {
-                uint32_t lf = leafw(wi);
-                uint32_t ro = Ro[sm.woff[l] + wi];
-                uint32_t pr = lf & ~ro, gh = 0;
-                if (rf) {
-                    pr |= dilate([&](int j) { return fold_at(pf, l + 1, j); }, l, wi, 1, d.bc) & ~ro;
-                    gh = dilate(leafw, l, wi, 2, d.bc) | dilate([&](int j) { return fold_at(gf, l + 1, j); }, l, wi, 1, d.bc);
+                for (int wp = tid; wp < (Wl >> 1); wp += TS) {
+                    uint32_t x = fold2(rl[2 * wp], rl[2 * wp + 1]);
+                    bool eL = (word_bc(rl, 2 * wp - 1, Wl, d.bc) >> 30) != 0u;  // children of parent 32 wp - 1
+                    bool eR = (word_bc(rl, 2 * wp + 2, Wl, d.bc) & 3u) != 0u;   // children of parent 32 wp + 32
+                    rp[wp] |= pairexpand(dilate1_edges(x, eL, eR));
                 }
-                LF[sm.woff[l] + wi] = lf & vb;
-                PR[sm.woff[l] + wi] = pr & vb;
-                GH[sm.woff[l] + wi] = gh & ~rl[wi] & vb;
-                // KEEP / REF of this level were last read by enlarge: clear for the next step
-                keep[sm.woff[l] + wi] = 0u;
-                ref[sm.woff[l] + wi] = 0u;
+            }
+            const uint32_t *rol = Ro + sm.woff[l];
+            uint32_t *lfl = LF + sm.woff[l], *prl = PR + sm.woff[l], *ghl = GH + sm.woff[l];
+            if (l == d.Jmax) {
+                for (int wi = tid; wi < Wl; wi += TS) {
+                    uint32_t r = rl[wi];
+                    lfl[wi] = r;
+                    prl[wi] = r & ~rol[wi];
+                    ghl[wi] = 0u;
+                }
+            } else {
+                const int Wc = Wl << 1;
+                const uint32_t *rc = Rn + sm.woff[l + 1], *pc = PR + sm.woff[l + 1], *gc = GH + sm.woff[l + 1];
+                for (int wi = tid; wi < Wl; wi += TS) {
+                    uint32_t r = rl[wi], ro = rol[wi];
+                    uint32_t lf = r & ~fold2(rc[2 * wi], rc[2 * wi + 1]);
+                    // leaf bits of cells 30, 31 of the left word and 0, 1 of the right word
+                    uint32_t lfL = (word_bc(rl, wi - 1, Wl, d.bc) >> 30) & ~fold_low2(word_bc(rc, 2 * wi - 1, Wc, d.bc) >> 28);
+                    uint32_t lfR = (word_bc(rl, wi + 1, Wl, d.bc) & 3u) & ~fold_low2(word_bc(rc, 2 * wi + 2, Wc, d.bc) & 15u);
+                    uint32_t gw = lf | (lf << 1) | (lf << 2) | (lf >> 1) | (lf >> 2);
+                    gw |= (lfL ? 1u : 0u) | ((lfL & 2u) ? 2u : 0u);                    // from cells 30, 31 on the left
+                    gw |= (lfR ? 0x80000000u : 0u) | ((lfR & 1u) ? 0x40000000u : 0u);  // from cells 0, 1 on the right
+                    uint32_t p = fold2(pc[2 * wi], pc[2 * wi + 1]);
+                    uint32_t pd = dilate1_edges(p, (word_bc(pc, 2 * wi - 1, Wc, d.bc) >> 30) != 0u,
+                                                (word_bc(pc, 2 * wi + 2, Wc, d.bc) & 3u) != 0u);
+                    uint32_t g = fold2(gc[2 * wi], gc[2 * wi + 1]);
+                    uint32_t gd = dilate1_edges(g, (word_bc(gc, 2 * wi - 1, Wc, d.bc) >> 30) != 0u,
+                                                (word_bc(gc, 2 * wi + 2, Wc, d.bc) & 3u) != 0u);
+                    lfl[wi] = lf;
+                    prl[wi] = (lf | pd) & ~ro;
+                    ghl[wi] = (gw | gd) & ~r;
+                }
             }
             sync();
         }
+        if (tid == 0)
+            for (int l = d.Jmax < 5 ? d.Jmax : 5; l >= d.Jmin; --l) small_level(Rn, Ro, l, grade);
+        sync();
+    }
+
+    // one level of at most 32 cells (a single word), grading of level l-1 and marks of level l
+    __device__ void small_level(uint32_t *Rn, const uint32_t *Ro, int l, bool grade) {
+        uint32_t *LF = mask(M_LEAF), *PR = mask(M_PRED), *GH = mask(M_GH);
+        const uint32_t *rl = Rn + sm.woff[l];
+        if (grade && l > d.Jmin + 1) {
+            uint32_t *rp = Rn + sm.woff[l - 1];
+            rp[0] |= pairexpand(dilate([&](int j) { return fold_at(rl, l, j); }, l - 1, 0, 1, d.bc)) & valid_bits(l - 1);
+        }
+        const uint32_t *rf = l < d.Jmax ? Rn + sm.woff[l + 1] : nullptr;
+        const uint32_t *pf = l < d.Jmax ? PR + sm.woff[l + 1] : nullptr;
+        const uint32_t *gf = l < d.Jmax ? GH + sm.woff[l + 1] : nullptr;
+        const uint32_t vb = valid_bits(l);
+        auto leafw = [&](int j) { return rf ? (rl[j] & ~fold_at(rf, l + 1, j)) : rl[j]; };
+        uint32_t lf = leafw(0);
+        uint32_t ro = Ro[sm.woff[l]];
+        uint32_t pr = lf & ~ro, gh = 0;
+        if (rf) {
+            pr |= dilate([&](int j) { return fold_at(pf, l + 1, j); }, l, 0, 1, d.bc) & ~ro;
+            gh = dilate(leafw, l, 0, 2, d.bc) | dilate([&](int j) { return fold_at(gf, l + 1, j); }, l, 0, 1, d.bc);
+        }
+        LF[sm.woff[l]] = lf & vb;
+        PR[sm.woff[l]] = pr & vb;
+        GH[sm.woff[l]] = gh & ~rl[0] & vb;
     }
 
     // ---- A5: list compaction -------------------------------------------------
@@ -571,20 +663,35 @@ struct Worker {
             for (int L = 0; L < NLIST; ++L) sm.seg[L][d.Jmax + 1] = sm.scan_tot[L];
             sm.nleaf = sm.scan_tot[L_LEAF];
         }
+        // the PRED / GH words are consumed: as KEEP / REF they must start the next step at zero
+        uint32_t *pr = mask(M_PRED), *gh = mask(M_GH);
+        for (int g = tid; g < d.Wtot; g += TS) {
+            pr[g] = 0u;
+            gh[g] = 0u;
+        }
         sync();
     }
 
     // ---- A6 / S3: prediction of listed cells, coarse to fine -----------------
+    __device__ __forceinline__ void predict_level(const uint32_t *lst, int L, int l) {
+        int b = sm.seg[L][l], e = sm.seg[L][l + 1];
+        for (int i = b + tid; i < e; i += TS) {
+            long long k = lst[i] & KMASK;
+            T v[QMAX];
+#pragma unroll
+            for (int h = 0; h < QMAX; ++h)
+                if (h < q) v[h] = predict<T>(row(h, l - 1), k >> 1, (int)(k & 1), l - 1, d.bc);
+#pragma unroll
+            for (int h = 0; h < QMAX; ++h)
+                if (h < q) row(h, l)[k] = v[h];
+        }
+    }
+
     __device__ void predict_fill(int L) {
         const uint32_t *lst = list(L);
         for (int l = d.Jmin + 1; l <= d.Jmax; ++l) {
-            int b = sm.seg[L][l], e = sm.seg[L][l + 1];
-            if (b == e) continue;
-            for (int i = b + tid; i < e; i += TS) {
-                long long k = lst[i] & KMASK;
-#pragma unroll
-                for (int h = 0; h < Q; ++h) row(h, l)[k] = predict<T>(row(h, l - 1), k >> 1, (int)(k & 1), l - 1, d.bc);
-            }
+            if (sm.seg[L][l] == sm.seg[L][l + 1]) continue;
+            predict_level(lst, L, l);
             sync();
         }
     }
@@ -617,62 +724,48 @@ struct Worker {
 
     // ---- one step of the adaptive scheme on the current mesh -----------------
     __device__ void lbm_step() {
-        const uint32_t *leaves = list(L_LEAF);
-        int nl = sm.nleaf;
         tick(NPHASE);
-        // S1 leaves collision
-        for (int i = tid; i < nl; i += TS) {
-            uint32_t ent = leaves[i];
-            int l = ent >> KBITS;
-            long long k = ent & KMASK;
-            T f[Q];
-#pragma unroll
-            for (int h = 0; h < Q; ++h) f[h] = row(h, l)[k];
-            collide<T, NF>(d, f);
-#pragma unroll
-            for (int h = 0; h < Q; ++h) row(h, l)[k] = f[h];
-        }
+        collide_all();          // S1
         sync();
         tick(T_COLLIDE);
-        upsweep();             // S2
+        upsweep();              // S2
         tick(T_UPSWEEP_S);
-        predict_fill(L_GH);    // S3
+        predict_fill(L_GH);     // S3
         tick(T_GHOSTS);
-        reconstruct_edges();   // S4
+        reconstruct_edges();    // S4
         sync();
         tick(T_RECON);
-        stream_and_audit();    // S5
+        stream_and_audit();     // S5
         tick(T_STREAM);
     }
 
     // S4: first / last finest-cell values of every leaf -> Phi
     __device__ void reconstruct_edges() {
-        const uint32_t *leaves = list(L_LEAF);
         const uint32_t *R = mask(sm.cur);
-        const long long N = d.N;
-        const int bc = d.bc;
+        const uint32_t *leaves = list(L_LEAF);
         for (int i = tid; i < sm.nleaf; i += TS) {
             uint32_t ent = leaves[i];
             int l = ent >> KBITS;
             long long k = ent & KMASK;
-            int dj = d.Jmax - l;
-            long long nl = 1LL << l;
-            bool at_left = bc == 1 && k == 0, at_right = bc == 1 && k == nl - 1;
+            const int dj = d.Jmax - l;
+            const long long nl = 1LL << l;
+            bool at_left = d.bc == 1 && k == 0, at_right = d.bc == 1 && k == nl - 1;
             bool fin_l = false, fin_r = false;
             if (dj > 0) {
                 const uint32_t *rf = R + sm.woff[l + 1];
                 if (!at_left) {
-                    long long c = 2 * wrapc(k - 1, l, bc);
+                    long long c = 2 * wrapc(k - 1, l, d.bc);
                     fin_l = (rf[c >> 5] >> (c & 31)) & 1u;
                 }
                 if (!at_right) {
-                    long long c = 2 * wrapc(k + 1, l, bc);
+                    long long c = 2 * wrapc(k + 1, l, d.bc);
                     fin_r = (rf[c >> 5] >> (c & 31)) & 1u;
                 }
             }
             const T *cf = tab.cf[dj], *t1 = tab.t1[dj], *bf = tab.bf[dj];
 #pragma unroll
-            for (int h = 0; h < Q; ++h) {
+            for (int h = 0; h < QMAX; ++h) {
+                if (h >= q) break;
                 const T *r = row(h, l);
                 const bool plus = (h & 1) == 0;  // velocity +lambda
                 bool need_first = !plus || at_left, need_last = plus || at_right;
@@ -680,7 +773,7 @@ struct Worker {
                 if (dj == 0) {
                     rfirst = rlast = r[k];
                 } else {
-                    T vm1 = r[wrapc(k - 1, l, bc)], v0 = r[k], vp1 = r[wrapc(k + 1, l, bc)];
+                    T vm1 = r[wrapc(k - 1, l, d.bc)], v0 = r[k], vp1 = r[wrapc(k + 1, l, d.bc)];
                     T tt = T(C1) * (vp1 - vm1);
                     T pe = v0 + tt, po = v0 - tt;  // children of the leaf
                     const T *rf = row(h, l + 1);
@@ -688,32 +781,32 @@ struct Worker {
                         if (at_left) {
                             rfirst = bf[0] * v0 + bf[1] * vp1;
                         } else if (fin_l) {
-                            long long c = 2 * wrapc(k - 1, l, bc);
+                            long long c = 2 * wrapc(k - 1, l, d.bc);
                             rfirst = dot4(t1[0], rf[c], t1[1], rf[c + 1], t1[2], pe, t1[3], po);
                         } else {
-                            rfirst = dot4(cf[0], r[wrapc(k - 2, l, bc)], cf[1], vm1, cf[2], v0, cf[3], vp1);
+                            rfirst = dot4(cf[0], r[wrapc(k - 2, l, d.bc)], cf[1], vm1, cf[2], v0, cf[3], vp1);
                         }
                     }
                     if (need_last) {
                         if (at_right) {
                             rlast = bf[0] * v0 + bf[1] * vm1;
                         } else if (fin_r) {
-                            long long c = 2 * wrapc(k + 1, l, bc);
+                            long long c = 2 * wrapc(k + 1, l, d.bc);
                             rlast = dot4(t1[3], pe, t1[2], po, t1[1], rf[c], t1[0], rf[c + 1]);
                         } else {
-                            rlast = dot4(cf[3], vm1, cf[2], v0, cf[1], vp1, cf[0], r[wrapc(k + 2, l, bc)]);
+                            rlast = dot4(cf[3], vm1, cf[2], v0, cf[1], vp1, cf[0], r[wrapc(k + 2, l, d.bc)]);
                         }
                     }
                 }
-                T *ph = Phi + (long long)h * (N + 1);
+                T *ph = Phi + (long long)h * (d.N + 1);
                 if (plus) {
                     long long ix = (k + 1) << dj;
-                    if (bc == 0) ix &= N - 1;
+                    if (d.bc == 0) ix &= d.N - 1;
                     ph[ix] = rlast;
                     if (at_left) ph[0] = rfirst;
                 } else {
                     ph[k << dj] = rfirst;
-                    if (at_right) ph[N] = rlast;
+                    if (at_right) ph[d.N] = rlast;
                 }
             }
         }
@@ -740,10 +833,7 @@ struct Worker {
     // S5: f^{n+1} = f* + sigma 2^-dj (Phi[first] - Phi[next]); FP64 mass audit
     __device__ void stream_and_audit() {
         const uint32_t *leaves = list(L_LEAF);
-        const long long N = d.N;
-        double macc[NF];
-#pragma unroll
-        for (int j = 0; j < NF; ++j) macc[j] = 0.0;
+        double macc[3] = {0.0, 0.0, 0.0};
         bool bad = false;
         for (int i = tid; i < sm.nleaf; i += TS) {
             uint32_t ent = leaves[i];
@@ -751,34 +841,35 @@ struct Worker {
             long long k = ent & KMASK;
             int dj = d.Jmax - l;
             long long first = k << dj, next = (k + 1) << dj;
-            if (d.bc == 0) next &= N - 1;
+            if (d.bc == 0) next &= d.N - 1;
             const T w = (T)ldexpf(1.0f, -dj);
-            T fn[Q];
+            T fn[QMAX];
 #pragma unroll
-            for (int h = 0; h < Q; ++h) {
-                const T *ph = Phi + (long long)h * (N + 1);
-                T coef = (h & 1) ? -w : w;
-                T *r = row(h, l);
-                T v = r[k] + coef * (ph[first] - ph[next]);
-                bad |= !isfinite(v);
-                r[k] = v;
-                fn[h] = v;
-            }
+            for (int h = 0; h < QMAX; ++h)
+                if (h < q) {
+                    const T *ph = Phi + (long long)h * (d.N + 1);
+                    T coef = (h & 1) ? -w : w;
+                    T *r = row(h, l);
+                    T v = r[k] + coef * (ph[first] - ph[next]);
+                    bad |= !isfinite(v);
+                    r[k] = v;
+                    fn[h] = v;
+                }
             const double dx = sm.dx_l[l];
 #pragma unroll
-            for (int j = 0; j < NF; ++j) macc[j] += dx * ((double)fn[2 * j] + (double)fn[2 * j + 1]);
+            for (int j = 0; j < 3; ++j)
+                if (j < nf) macc[j] += dx * ((double)fn[2 * j] + (double)fn[2 * j + 1]);
         }
         if (bad) atomicOr(&sm.status, (int)ST_NONFINITE);
-        double tot[NF];
-#pragma unroll
-        for (int j = 0; j < NF; ++j) tot[j] = team_sum(macc[j], j);
+        double tot[3];
+        for (int j = 0; j < nf; ++j) tot[j] = team_sum(macc[j], j);
         if (tid == 0) {
             double dxJ = sm.dx_l[d.Jmax];
-            for (int j = 0; j < NF; ++j) {
+            for (int j = 0; j < nf; ++j) {
                 double flux = 0.0;
                 if (d.bc == 1) {
-                    const T *pp = Phi + (long long)(2 * j) * (N + 1), *pm = Phi + (long long)(2 * j + 1) * (N + 1);
-                    flux = dxJ * (((double)pp[0] - (double)pp[N]) - ((double)pm[0] - (double)pm[N]));
+                    const T *pp = Phi + (long long)(2 * j) * (d.N + 1), *pm = Phi + (long long)(2 * j + 1) * (d.N + 1);
+                    flux = dxJ * (((double)pp[0] - (double)pp[d.N]) - ((double)pm[0] - (double)pm[d.N]));
                 }
                 double res = fabs(tot[j] - sm.mass[j] - flux);
                 sm.audit = fmax(sm.audit, res);
@@ -800,14 +891,11 @@ struct Worker {
             mask(M_KEEP)[g] = 0u;
             mask(M_REF)[g] = 0u;
         }
-        const long long N = d.N;
-        for (long long k = tid; k < N; k += TS) {
-            double mc[NF], f[Q];
-#pragma unroll
-            for (int j = 0; j < NF; ++j) mc[j] = mcons[j * N + k];
+        for (long long k = tid; k < d.N; k += TS) {
+            double mc[3], f[QMAX];
+            for (int j = 0; j < nf; ++j) mc[j] = mcons[j * d.N + k];
             equilibrium_populations<NF>(d, mc, f);
-#pragma unroll
-            for (int h = 0; h < Q; ++h) row(h, d.Jmax)[k] = (T)f[h];
+            for (int h = 0; h < q; ++h) row(h, d.Jmax)[k] = (T)f[h];
         }
         if (tid == 0) sm.cur = M_R0;
         sync();
@@ -828,7 +916,7 @@ struct Worker {
             mask(M_KEEP)[g] = 0u;
             mask(M_REF)[g] = 0u;
         }
-        for (long long c = tid; c < (long long)Q * d.S; c += TS) V[c] = (T)vals[c];
+        for (long long c = tid; c < (long long)q * d.S; c += TS) V[c] = (T)vals[c];
         if (tid == 0) sm.cur = M_R0;
         sync();
         finish_init();
@@ -840,22 +928,18 @@ struct Worker {
         build_lists(R);
         // FP64 totals of the initial leaves
         const uint32_t *leaves = list(L_LEAF);
-        double macc[NF];
-#pragma unroll
-        for (int j = 0; j < NF; ++j) macc[j] = 0.0;
+        double macc[3] = {0.0, 0.0, 0.0};
         for (int i = tid; i < sm.nleaf; i += TS) {
             uint32_t ent = leaves[i];
             int l = ent >> KBITS;
             long long k = ent & KMASK;
             double dx = sm.dx_l[l];
-#pragma unroll
-            for (int j = 0; j < NF; ++j) macc[j] += dx * ((double)row(2 * j, l)[k] + (double)row(2 * j + 1, l)[k]);
+            for (int j = 0; j < nf; ++j) macc[j] += dx * ((double)row(2 * j, l)[k] + (double)row(2 * j + 1, l)[k]);
         }
-        double tot[NF];
-#pragma unroll
-        for (int j = 0; j < NF; ++j) tot[j] = team_sum(macc[j], j);
+        double tot[3];
+        for (int j = 0; j < nf; ++j) tot[j] = team_sum(macc[j], j);
         if (tid == 0) {
-            for (int j = 0; j < NF; ++j) sm.mass[j] = tot[j];
+            for (int j = 0; j < nf; ++j) sm.mass[j] = tot[j];
             sm.audit = 0.0;
             sm.status = 0;
             sm.near_ties = 0;
@@ -875,14 +959,11 @@ struct Worker {
             const uint32_t *rl = R + sm.woff[l];
             for (long long k = tid; k < n; k += TS)
                 if (!((rl[k >> 5] >> (k & 31)) & 1u))
-#pragma unroll
-                    for (int h = 0; h < Q; ++h) row(h, l)[k] = predict<T>(row(h, l - 1), k >> 1, (int)(k & 1), l - 1, d.bc);
+                    for (int h = 0; h < q; ++h) row(h, l)[k] = predict<T>(row(h, l - 1), k >> 1, (int)(k & 1), l - 1, d.bc);
             sync();
         }
-        const long long N = d.N;
-        for (long long k = tid; k < N; k += TS)
-#pragma unroll
-            for (int j = 0; j < NF; ++j) out[j * N + k] = (double)row(2 * j, d.Jmax)[k] + (double)row(2 * j + 1, d.Jmax)[k];
+        for (long long k = tid; k < d.N; k += TS)
+            for (int j = 0; j < nf; ++j) out[j * d.N + k] = (double)row(2 * j, d.Jmax)[k] + (double)row(2 * j + 1, d.Jmax)[k];
         sync();
     }
 };
@@ -988,10 +1069,7 @@ __device__ void run_team(TeamSmem<T> &sm, const Tables<T> &tab, BlockScratch &bx
             smask[M_KEEP * W + g] = 0u;
             smask[M_REF * W + g] = 0u;
         }
-        if constexpr (TS == 32)
-            __syncwarp();
-        else
-            __syncthreads();
+        __syncthreads();
     }
     switch (sm.d.nf) {
     case 1: run_instance<T, 1, TS>(sm, tab, bx, a, tid, masks); break;
@@ -1006,10 +1084,8 @@ __device__ void run_team(TeamSmem<T> &sm, const Tables<T> &tab, BlockScratch &bx
     store_instance<T, TS>(sm, tid);
 }
 
-// Persistent kernel.  The queue holds instances largest first; block-team
-// instances come first.  A block takes instances one at a time while they are
-// block-team instances; at the first warp-team instance it switches to warp
-// mode for good and every warp pulls instances on its own.
+// Persistent kernel: each block takes instances from the queue (largest first)
+// and advances one at a time with all its threads.
 template <typename T, int NT, int MINB>
 __global__ void __launch_bounds__(NT, MINB) mr_persistent(LaunchArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -1022,33 +1098,13 @@ __global__ void __launch_bounds__(NT, MINB) mr_persistent(LaunchArgs a) {
         uint32_t *dst = (uint32_t *)&bs.tab;
         for (int i = threadIdx.x; i < (int)(sizeof(Tables<T>) / 4); i += NT) dst[i] = src[i];
     }
-    int idx;
     for (;;) {
         if (threadIdx.x == 0) bs.idx = atomicAdd(a.queue, 1);
         __syncthreads();
-        idx = bs.idx;
+        const int idx = bs.idx;
         __syncthreads();
         if (idx >= a.n) return;
-        const InstDesc &dg = a.descs[a.order[idx]];
-        if (!dg.team) break;
-        run_team<T, NT>(bs.team[0], bs.tab, bs.scratch, a, dg, threadIdx.x, smask, a.smem_mask_words);
-    }
-    // warp mode: warp 0 keeps idx, the other warps pull their own
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    TeamSmem<T> &sm = bs.team[warp];
-    int my = idx;
-    if (warp != 0) {
-        if (lane == 0) sm.idx = atomicAdd(a.queue, 1);
-        __syncwarp();
-        my = sm.idx;
-        __syncwarp();
-    }
-    while (my < a.n) {
-        run_team<T, 32>(sm, bs.tab, bs.scratch, a, a.descs[a.order[my]], lane, nullptr, 0);
-        if (lane == 0) sm.idx = atomicAdd(a.queue, 1);
-        __syncwarp();
-        my = sm.idx;
-        __syncwarp();
+        run_team<T, NT>(bs.team, bs.tab, bs.scratch, a, a.descs[a.order[idx]], threadIdx.x, smask, a.smem_mask_words);
     }
 }
 

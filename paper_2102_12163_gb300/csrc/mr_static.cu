@@ -112,7 +112,6 @@ extern "C" mr_status mr_run_static(const mr_instance_desc *desc, int precision, 
     h.eq = d.eq;
     h.nf = nf;
     h.mu_bar = d.mu_bar;
-    h.team = 1;
     h.Wtot = W;
     h.eps = d.eps;
     h.a = d.a;

@@ -54,7 +54,7 @@ def test_argument_validation():
     assert small > 0
     # stepping before a workspace is bound is refused, not run
     assert L.mr_advance(h, 1) == capi.MR_ERR_STATE
-    assert L.mr_set_launch(h, 100, 0, -1) == capi.MR_ERR_ARG
+    assert L.mr_set_launch(h, 100, 0) == capi.MR_ERR_ARG
     assert L.mr_destroy(h) == capi.MR_OK
     # workspace grows with the finest level
     assert L.mr_mesh_init(ctypes.byref(h), 2, 12, 1, 1e-4, -1.0, 1.0, 0, 0, 0) == capi.MR_OK

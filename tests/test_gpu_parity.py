@@ -289,22 +289,3 @@ def test_nonfinite_populations_are_reported():
     with pytest.raises(MRError) as ei:
         s.sync()
     assert ei.value.code == -4
-
-
-@pytest.mark.parametrize("precision", [MR_FP64, MR_FP32_MIXED])
-def test_warp_teams_and_block_teams_agree(precision):
-    """The same instances advanced by one warp each and by a whole block each
-    give identical meshes and populations."""
-    from paper_2102_12163_gb300 import MRLBM
-
-    insts = W.batch(n=20, seed=21, Jmax_range=(6, 12))
-    res = []
-    for tj in (0, 99):  # 0: every instance gets a block; 99: every instance gets a warp
-        s = MRLBM(insts, precision=precision, block=256, block_team_jmax=tj)
-        s.set_initial()
-        s.advance(12)
-        s.sync()
-        res.append([(s.tree(i), s.leaves(i)[2]) for i in range(len(insts))])
-    for (ra, fa), (rb, fb) in zip(*res):
-        assert np.array_equal(ra, rb)
-        assert np.array_equal(fa, fb)
