@@ -62,8 +62,9 @@ SIGNATURES = {
 _lib = None
 
 
-PHASES = ["projection (adapt)", "details + threshold", "enlargement", "grading + marking", "list compaction",
-          "data transfer", "collision", "projection (step)", "ghosts", "reconstruction", "stream + audit"]
+PHASES = ["projection (adapt)", "details + threshold", "enlargement", "grading + marking",
+          "grading (small levels)", "list counts + scan", "list writes", "data transfer", "collision",
+          "projection (step)", "ghosts", "reconstruction", "stream + audit"]
 
 
 def load(build_if_missing: bool = True, profile: bool = False) -> ctypes.CDLL:

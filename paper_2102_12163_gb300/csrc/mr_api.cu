@@ -58,6 +58,7 @@ struct mr_ctx {
     bool bound = false, initialised = false;
     int block = 0, grid = 0, grid_req = 0, sms = 0;
     int mask_cap = 0;    // words per bitmask a block team keeps in shared memory
+    bool order_by_fields = true;
     long long launches = 0;
     std::string err;
 
@@ -371,10 +372,13 @@ mr_status mr_bind(mr_ctx *c, void *ws, size_t bytes, void *stream) {
         c->block = n == 1 ? (jmax >= 12 ? 1024 : 512) : 256;
     }
     c->hdesc = dd;
-    // processing order: largest instances first (nf 2^Jmax as the cost estimate)
+    // processing order: by field count (blocks resident together then run the
+    // same scheme's code, which keeps the instruction cache warm), then largest
+    // first (nf 2^Jmax as the cost estimate)
     std::vector<int> order(n), ident(n);
     for (int i = 0; i < n; ++i) order[i] = ident[i] = i;
     std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
+        if (c->order_by_fields && dd[x].nf != dd[y].nf) return dd[x].nf > dd[y].nf;
         double cx = (double)dd[x].nf * std::ldexp(1.0, dd[x].Jmax);
         double cy = (double)dd[y].nf * std::ldexp(1.0, dd[y].Jmax);
         return cx > cy;

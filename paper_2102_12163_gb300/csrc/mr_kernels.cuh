@@ -540,34 +540,54 @@ struct Worker {
             }
             sync();
         }
+        tick(T_GRADE);
         if (tid == 0)
             for (int l = d.Jmax < 5 ? d.Jmax : 5; l >= d.Jmin; --l) small_level(Rn, Ro, l, grade);
         sync();
     }
 
-    // one level of at most 32 cells (a single word), grading of level l-1 and marks of level l
+    // dilation by r cells inside a level of n <= 32 cells held in one word
+    __device__ __forceinline__ uint32_t dil_small(uint32_t x, int n, int r) const {
+        const uint32_t vb = n == 32 ? 0xFFFFFFFFu : ((1u << n) - 1u);
+        uint32_t out = x;
+        for (int s = 1; s <= r; ++s) {
+            if (d.bc == 0)
+                out |= ((x << s) | (x >> (n - s)) | (x >> s) | (x << (n - s))) & vb;
+            else
+                out |= ((x << s) & vb) | (x >> s);
+        }
+        return out;
+    }
+    // parent bits (n of them) of the child level l+1 of a level of n <= 32 cells
+    __device__ __forceinline__ uint32_t fold_small(const uint32_t *child, int l) const {
+        return l + 1 >= 6 ? fold2(child[0], child[1]) : fold2(child[0], 0u);
+    }
+
+    // one level of at most 32 cells (a single word): grading of level l-1 and
+    // marks of level l, as in the word-wise sweep above
     __device__ void small_level(uint32_t *Rn, const uint32_t *Ro, int l, bool grade) {
         uint32_t *LF = mask(M_LEAF), *PR = mask(M_PRED), *GH = mask(M_GH);
-        const uint32_t *rl = Rn + sm.woff[l];
+        const int n = 1 << l, o = sm.woff[l];
+        const uint32_t vb = n == 32 ? 0xFFFFFFFFu : ((1u << n) - 1u);
+        const uint32_t r = Rn[o];
         if (grade && l > d.Jmin + 1) {
-            uint32_t *rp = Rn + sm.woff[l - 1];
-            rp[0] |= pairexpand(dilate([&](int j) { return fold_at(rl, l, j); }, l - 1, 0, 1, d.bc)) & valid_bits(l - 1);
+            const int np = n >> 1;
+            const uint32_t vbp = (1u << np) - 1u;
+            Rn[sm.woff[l - 1]] |= pairexpand(dil_small(fold2(r, 0u), np, 1)) & vbp;
         }
-        const uint32_t *rf = l < d.Jmax ? Rn + sm.woff[l + 1] : nullptr;
-        const uint32_t *pf = l < d.Jmax ? PR + sm.woff[l + 1] : nullptr;
-        const uint32_t *gf = l < d.Jmax ? GH + sm.woff[l + 1] : nullptr;
-        const uint32_t vb = valid_bits(l);
-        auto leafw = [&](int j) { return rf ? (rl[j] & ~fold_at(rf, l + 1, j)) : rl[j]; };
-        uint32_t lf = leafw(0);
-        uint32_t ro = Ro[sm.woff[l]];
-        uint32_t pr = lf & ~ro, gh = 0;
-        if (rf) {
-            pr |= dilate([&](int j) { return fold_at(pf, l + 1, j); }, l, 0, 1, d.bc) & ~ro;
-            gh = dilate(leafw, l, 0, 2, d.bc) | dilate([&](int j) { return fold_at(gf, l + 1, j); }, l, 0, 1, d.bc);
+        const uint32_t ro = Ro[o];
+        uint32_t lf = r, pr, gh = 0u;
+        if (l < d.Jmax) {
+            const int oc = sm.woff[l + 1];
+            lf = r & ~fold_small(Rn + oc, l);
+            pr = (lf | dil_small(fold_small(PR + oc, l), n, 1)) & ~ro;
+            gh = (dil_small(lf, n, 2) | dil_small(fold_small(GH + oc, l), n, 1)) & ~r;
+        } else {
+            pr = lf & ~ro;
         }
-        LF[sm.woff[l]] = lf & vb;
-        PR[sm.woff[l]] = pr & vb;
-        GH[sm.woff[l]] = gh & ~rl[0] & vb;
+        LF[o] = lf & vb;
+        PR[o] = pr & vb;
+        GH[o] = gh & vb;
     }
 
     // ---- A5: list compaction -------------------------------------------------
@@ -638,6 +658,7 @@ struct Worker {
             for (int L = 0; L < NLIST; ++L) cnt[L] += __popc(m[L]);
         }
         team_scan(cnt, off);
+        tick(T_LISTS_COUNT);
         for (int g = g0; g < g1; ++g) {
             int l, wi;
             level_of_word(sm, g, l, wi);
@@ -710,7 +731,7 @@ struct Worker {
         sync();
         tick(T_ENLARGE);
         grade_and_mark(Rn, Ro, true);
-        tick(T_GRADE);
+        tick(T_GRADE_SMALL);
         build_lists(Rn);
         tick(T_LISTS);
         predict_fill(L_PRED);
@@ -882,7 +903,7 @@ struct Worker {
 
     // ---- initial state -------------------------------------------------------
     // full tree, populations at equilibrium of the conserved moments (staged m_cons)
-    __device__ void init_full(const double *mcons) {
+    __device__ __noinline__ void init_full(const double *mcons) {
         uint32_t *R = mask(M_R0);
         for (int g = tid; g < d.Wtot; g += TS) {
             int l, wi;
@@ -903,7 +924,7 @@ struct Worker {
     }
 
     // arbitrary graded tree (one byte per cell) and values
-    __device__ void init_state(const unsigned char *Rb, const double *vals) {
+    __device__ __noinline__ void init_state(const unsigned char *Rb, const double *vals) {
         uint32_t *R = mask(M_R0);
         for (int g = tid; g < d.Wtot; g += TS) {
             int l, wi;
@@ -922,7 +943,7 @@ struct Worker {
         finish_init();
     }
 
-    __device__ void finish_init() {
+    __device__ __noinline__ void finish_init() {
         uint32_t *R = mask(sm.cur);
         grade_and_mark(R, R, false);  // PRED empty: the tree is its own old tree
         build_lists(R);
@@ -950,7 +971,7 @@ struct Worker {
     }
 
     // ---- multiresolution reconstruction on the finest level (measurement) ----
-    __device__ void finest(double *out) {
+    __device__ __noinline__ void finest(double *out) {
         upsweep();
         sync();
         const uint32_t *R = mask(sm.cur);
