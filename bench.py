@@ -57,15 +57,17 @@ def source_hash() -> str:
     return h.hexdigest()[:16]
 
 
-def profiled_traffic(workload: str, precision: str):
-    """DRAM bytes per launch from the committed ncu summary, if it was taken on
-    the current kernel source (else None)."""
+def profiled_traffic(workload: str, precision: str, steps: int, warmup: int, instances: int):
+    """DRAM bytes per launch from the committed ncu record (profiles/traffic.json),
+    if it was taken on the current kernel source and the same launch (else None)."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         with open(path) as fh:
             j = json.load(fh)
         e = j[f"{workload}:{precision}"]
-        if e.get("source_hash") != source_hash():
+        if e.get("source_hash") != source_hash() or e.get("steps") != steps or e.get("warmup") != warmup:
+            return None
+        if workload == "batch" and instances != 4096:
             return None
         return e
     except Exception:
@@ -87,7 +89,7 @@ class ClockSampler:
     def __enter__(self):
         try:
             self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
-                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                          "--format=csv,noheader,nounits", "-lms", "50"],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
@@ -262,19 +264,66 @@ def e2e(s, steps: int):
             "d2h_bytes_per_step": (mass.numel() * 8 + nleaf.numel() * 4) / steps, "seconds": t}
 
 
+# --------------------------------------------------------------------------- accuracy (untimed)
+
+def accuracy(insts, steps: int, every: int = 256):
+    """L1 error of the conserved moments against the uniform reference scheme,
+    FP32 at eps versus FP64 at eps and at 2 eps, on a sample of the workload.
+    The reference is the FP64 path at eps = 0 (the adaptive scheme on the full
+    tree is the reference scheme on the finest lattice)."""
+    import numpy as np
+
+    from paper_2102_12163_gb300 import MR_FP32_MIXED, MR_FP64, MRLBM
+
+    sample = insts[::every] if len(insts) > every else insts
+
+    def run(prec, scale):
+        ins = [i.with_(eps=i.eps * scale) for i in sample]
+        for a, b in zip(ins, sample):
+            a.m0 = b.m0
+        s = MRLBM(ins, precision=prec)
+        s.set_initial()
+        s.advance(steps)
+        s.sync()
+        out = [s.finest(i) for i in range(len(ins))]
+        s.close()
+        return out
+
+    ref = run(MR_FP64, 0.0)
+    f64, f64x2, f32 = run(MR_FP64, 1.0), run(MR_FP64, 2.0), run(MR_FP32_MIXED, 1.0)
+    rows = []
+    for i, inst in enumerate(sample):
+        d = lambda m: float(inst.dx * np.abs(m - ref[i]).sum())  # noqa: E731  (weighted l1, all fields)
+        rows.append((d(f32[i]), d(f64[i]), d(f64x2[i]), float(np.max(np.abs(f32[i] - f64[i])))))
+    r = np.array(rows)
+    ok = r[:, 0] <= r[:, 2] * (1 + 1e-12) + 1e-15
+    return {
+        "instances": len(sample), "steps": steps,
+        "delta_l1_fp32_eps_median": float(np.median(r[:, 0])),
+        "delta_l1_fp64_eps_median": float(np.median(r[:, 1])),
+        "delta_l1_fp64_2eps_median": float(np.median(r[:, 2])),
+        "fp32_within_fp64_at_2eps": f"{int(ok.sum())}/{len(sample)}",
+        "fp32_vs_fp64_linf_max": float(r[:, 3].max()),
+        "reference": "uniform finest-lattice scheme (FP64 path at eps = 0)",
+    }
+
+
 # --------------------------------------------------------------------------- main
 
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=512)
+    ap.add_argument("--steps", type=int, default=1024)
     ap.add_argument("--warmup", type=int, default=16)
     ap.add_argument("--instances", type=int, default=4096, help="batch size (smaller only for profiling)")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="batch", choices=["batch", "advection", "burgers", "shallow", "sod"])
     ap.add_argument("--block", type=int, default=None)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-fp64", action="store_true", help="same as --precision fp32")
+    ap.add_argument("--precision", default="both", choices=["both", "fp32", "fp64"],
+                    help="legs to time: the FP32 headline with FP64 beside it, or one of them")
+    ap.add_argument("--no-accuracy", action="store_true")
     args = ap.parse_args()
 
     rank = int(os.environ.get("RANK", "0"))
@@ -312,9 +361,20 @@ def main():
 
     from paper_2102_12163_gb300 import MR_FP32_MIXED, MR_FP64
 
-    r32 = run_gpu(insts, MR_FP32_MIXED, args.steps, args.warmup, rank, world, dist, args.block)
-    r64 = None if args.no_fp64 else run_gpu(insts, MR_FP64, args.steps, args.warmup, rank, world, dist, args.block)
-    ee = e2e(r32["solver"], args.steps)
+    if args.no_fp64:
+        args.precision = "fp32"
+    r32 = r64 = None
+    if args.precision in ("both", "fp32"):
+        r32 = run_gpu(insts, MR_FP32_MIXED, args.steps, args.warmup, rank, world, dist, args.block)
+    if args.precision in ("both", "fp64"):
+        r64 = run_gpu(insts, MR_FP64, args.steps, args.warmup, rank, world, dist, args.block)
+    head = r32 if r32 is not None else r64
+    head_prec = "fp32" if r32 is not None else "fp64"
+    ee = e2e(head["solver"], args.steps)
+
+    acc = None
+    if rank == 0 and not args.no_accuracy and args.workload == "batch":
+        acc = accuracy(insts, min(args.steps, 64))
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -329,26 +389,28 @@ def main():
 
     def roof(r, prec):
         achieved = r["bytes_alg"] / r["dt"] / 1e9
-        tr = profiled_traffic(args.workload, prec)
+        tr = profiled_traffic(args.workload, prec, args.steps, args.warmup, len(insts))
         return {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
                 "traffic": (tr["dram_bytes_per_launch"] if tr else None),
                 "peak_source": f"{hbm_src} HBM copy bandwidth (MEASURED_PEAKS.json)" if hbm_src == "measured"
                 else "fallback 6.8 TB/s", "algorithmic_bytes_per_update": 2 * r["qmean"] * (4 if prec == "fp32" else 8)}
 
     line = {
-        "metric": METRIC, "value": r32["updates"] / r32["dt"], "unit": UNIT, "n_gpus": world,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": r32["dt"] * 1e3 / args.steps,
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "metric": METRIC, "value": head["updates"] / head["dt"], "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": head["dt"] * 1e3 / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32" if head_prec == "fp32" else "f64", "data": "synthetic",
         "config": {"workload": desc, "instances_per_gpu": len(insts), "steps_per_launch": args.steps,
                    "l2": "inputs larger than L2 (per-GPU workspace of several GB)",
                    "precision": "FP32 populations, FP64 coarse-level detail test and mass audit"},
-        "roofline": roof(r32, "fp32"),
+        "roofline": roof(head, head_prec),
         "cpu_baseline": cpu,
         "e2e": ee,
-        "gpu_launches": r32["launches"],
-        "clocks": r32["clocks"],
+        "gpu_launches": head["launches"],
+        "clocks": head["clocks"],
+        "accuracy": acc,
     }
-    if r64:
+    if r64 is not None and r32 is not None:
         line["fp64"] = {"value": r64["updates"] / r64["dt"], "ms_per_step": r64["dt"] * 1e3 / args.steps,
                         "roofline": roof(r64, "fp64"), "gpu_launches": r64["launches"], "clocks": r64["clocks"]}
     print(json.dumps(line), flush=True)
