@@ -141,8 +141,9 @@ mr_status mr_get_finest(mr_ctx *ctx, int inst, double *m_finest);
 /* Complete tree membership R (S bytes, cell numbering of mr_set_state). */
 mr_status mr_get_tree(mr_ctx *ctx, int inst, unsigned char *R);
 
-/* FP64 conserved totals sum_leaves dx_l m_j (n values) and the largest
- * per-step residual |mass change - boundary flux| seen so far. */
+/* Conserved totals sum_leaves dx_l m_j (n values, returned in FP64; the FP32
+ * path accumulates them in float-float, relative error near 2^-44) and the
+ * largest per-step residual |mass change - boundary flux| seen so far. */
 mr_status mr_audit(mr_ctx *ctx, int inst, double *mass, double *residual);
 
 /* Per-instance summary in one copy: FP64 conserved totals (mass[3 * i + j],

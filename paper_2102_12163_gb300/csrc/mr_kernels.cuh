@@ -334,19 +334,72 @@ struct Worker {
     __device__ __forceinline__ uint32_t *list(int L) { return d.lists + d.list_off[L]; }
     __device__ __forceinline__ T *row(int h, int l) { return V + (long long)h * d.S + cell_off(l, d.Jmin); }
 
-    // sum over the team of a per-thread double
-    __device__ __forceinline__ double team_sum(double x, int j) {
+    // sums over the team of nf per-thread doubles, valid in thread 0 (one barrier)
+    __device__ __forceinline__ void team_sum(double (&x)[3]) {
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(FULL, x, o);
-        if constexpr (WARP) {
-            return __shfl_sync(FULL, x, 0);
-        } else {
-            if ((tid & 31) == 0) bx.red[j][tid >> 5] = x;
+        for (int j = 0; j < 3; ++j)
+            if (j < nf)
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) x[j] += __shfl_down_sync(FULL, x[j], o);
+        if constexpr (!WARP) {
+            if ((tid & 31) == 0)
+#pragma unroll
+                for (int j = 0; j < 3; ++j)
+                    if (j < nf) bx.red[j][tid >> 5] = x[j];
             sync();
-            double t = 0.0;
-            for (int w = 0; w < TS / 32; ++w) t += bx.red[j][w];
-            return t;
+            if (tid == 0)
+#pragma unroll
+                for (int j = 0; j < 3; ++j)
+                    if (j < nf) {
+                        double t = 0.0;
+                        for (int w = 0; w < TS / 32; ++w) t += bx.red[j][w];
+                        x[j] = t;
+                    }
         }
+    }
+
+    // float-float accumulation (hi + lo, error-free transformation TwoSum of
+    // Knuth): the FP32 path keeps its mass audit off the FP64 pipe
+    static __device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
+        s = a + b;
+        const float bb = s - a;
+        e = (a - (s - bb)) + (b - bb);
+    }
+    static __device__ __forceinline__ void ff_add(float &hi, float &lo, float xh, float xl) {
+        float s, e;
+        two_sum(hi, xh, s, e);
+        hi = s;
+        lo = lo + (xl + e);
+    }
+    // team sums of nf float-float pairs, as doubles valid in thread 0 (one barrier)
+    __device__ __forceinline__ void team_sum_ff(float (&hi)[3], float (&lo)[3], double (&out)[3]) {
+#pragma unroll
+        for (int j = 0; j < 3; ++j)
+            if (j < nf)
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) {
+                    const float h2 = __shfl_down_sync(FULL, hi[j], o), l2 = __shfl_down_sync(FULL, lo[j], o);
+                    ff_add(hi[j], lo[j], h2, l2);
+                }
+        if constexpr (!WARP) {
+            float2 *red = reinterpret_cast<float2 *>(&bx.red[0][0]);
+            if ((tid & 31) == 0)
+#pragma unroll
+                for (int j = 0; j < 3; ++j)
+                    if (j < nf) red[j * 32 + (tid >> 5)] = make_float2(hi[j], lo[j]);
+            sync();
+            if (tid == 0)
+#pragma unroll
+                for (int j = 0; j < 3; ++j)
+                    if (j < nf) {
+                        float h = 0.0f, l = 0.0f;
+                        for (int w = 0; w < TS / 32; ++w) ff_add(h, l, red[j * 32 + w].x, red[j * 32 + w].y);
+                        hi[j] = h;
+                        lo[j] = l;
+                    }
+        }
+#pragma unroll
+        for (int j = 0; j < 3; ++j) out[j] = (double)hi[j] + (double)lo[j];
     }
 
     // ---- projection of the internal cells of level l (Def. Projection operator)
@@ -851,10 +904,14 @@ struct Worker {
         }
     }
 
-    // S5: f^{n+1} = f* + sigma 2^-dj (Phi[first] - Phi[next]); FP64 mass audit
+    // S5: f^{n+1} = f* + sigma 2^-dj (Phi[first] - Phi[next]); mass audit.
+    // The totals sum dx_l (f+ + f-) over the leaves: FP64 in the FP64 path; in
+    // the FP32 path 2^-l (f+ + f-) is summed exactly per leaf into float-float
+    // partials (relative error near 2^-44) and scaled by b - a at the end.
     __device__ void stream_and_audit() {
         const uint32_t *leaves = list(L_LEAF);
         double macc[3] = {0.0, 0.0, 0.0};
+        float fhi[3] = {0.0f, 0.0f, 0.0f}, flo[3] = {0.0f, 0.0f, 0.0f};
         bool bad = false;
         for (int i = tid; i < sm.nleaf; i += TS) {
             uint32_t ent = leaves[i];
@@ -876,14 +933,30 @@ struct Worker {
                     r[k] = v;
                     fn[h] = v;
                 }
-            const double dx = sm.dx_l[l];
+            if constexpr (sizeof(T) == 8) {
+                const double dx = sm.dx_l[l];
 #pragma unroll
-            for (int j = 0; j < 3; ++j)
-                if (j < nf) macc[j] += dx * ((double)fn[2 * j] + (double)fn[2 * j + 1]);
+                for (int j = 0; j < 3; ++j)
+                    if (j < nf) macc[j] += dx * ((double)fn[2 * j] + (double)fn[2 * j + 1]);
+            } else {
+                const float sc = ldexpf(1.0f, -l);
+#pragma unroll
+                for (int j = 0; j < 3; ++j)
+                    if (j < nf) {
+                        float sj, ej;
+                        two_sum((float)fn[2 * j], (float)fn[2 * j + 1], sj, ej);
+                        ff_add(fhi[j], flo[j], sj * sc, ej * sc);
+                    }
+            }
         }
         if (bad) atomicOr(&sm.status, (int)ST_NONFINITE);
-        double tot[3];
-        for (int j = 0; j < nf; ++j) tot[j] = team_sum(macc[j], j);
+        if constexpr (sizeof(T) == 8) {
+            team_sum(macc);
+        } else {
+            team_sum_ff(fhi, flo, macc);
+            if (tid == 0)
+                for (int j = 0; j < nf; ++j) macc[j] *= d.b - d.a;
+        }
         if (tid == 0) {
             double dxJ = sm.dx_l[d.Jmax];
             for (int j = 0; j < nf; ++j) {
@@ -892,9 +965,9 @@ struct Worker {
                     const T *pp = Phi + (long long)(2 * j) * (d.N + 1), *pm = Phi + (long long)(2 * j + 1) * (d.N + 1);
                     flux = dxJ * (((double)pp[0] - (double)pp[d.N]) - ((double)pm[0] - (double)pm[d.N]));
                 }
-                double res = fabs(tot[j] - sm.mass[j] - flux);
+                double res = fabs(macc[j] - sm.mass[j] - flux);
                 sm.audit = fmax(sm.audit, res);
-                sm.mass[j] = tot[j];
+                sm.mass[j] = macc[j];
             }
             sm.steps += 1ULL;
         }
@@ -957,10 +1030,9 @@ struct Worker {
             double dx = sm.dx_l[l];
             for (int j = 0; j < nf; ++j) macc[j] += dx * ((double)row(2 * j, l)[k] + (double)row(2 * j + 1, l)[k]);
         }
-        double tot[3];
-        for (int j = 0; j < nf; ++j) tot[j] = team_sum(macc[j], j);
+        team_sum(macc);
         if (tid == 0) {
-            for (int j = 0; j < nf; ++j) sm.mass[j] = tot[j];
+            for (int j = 0; j < nf; ++j) sm.mass[j] = macc[j];
             sm.audit = 0.0;
             sm.status = 0;
             sm.near_ties = 0;
