@@ -172,7 +172,6 @@ struct TeamSmem {
     int seg[NLIST][MAXLEV + 2];
     double eps_l[MAXLEV + 1], big_l[MAXLEV + 1], dx_l[MAXLEV + 1];  // per level
     float eps_f[MAXLEV + 1], big_f[MAXLEV + 1];
-    int scan_tot[NLIST];
     double mass[3];
     double audit;
     unsigned long long updates, steps;
@@ -187,7 +186,7 @@ struct TeamSmem {
 
 // block-team scratch (scan partials and reduction slots of the warps)
 struct BlockScratch {
-    int scan_w[NLIST][32];
+    int scan_w[2][NLIST][32];
     double red[3][32];
 };
 
@@ -644,51 +643,6 @@ struct Worker {
     }
 
     // ---- A5: list compaction -------------------------------------------------
-    __device__ void team_scan(int (&v)[NLIST], int (&excl)[NLIST]) {
-        int lane = tid & 31, warp = tid >> 5;
-        int inc[NLIST];
-#pragma unroll
-        for (int L = 0; L < NLIST; ++L) {
-            int x = v[L];
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                int y = __shfl_up_sync(FULL, x, o);
-                if (lane >= o) x += y;
-            }
-            inc[L] = x;
-        }
-        if constexpr (WARP) {
-#pragma unroll
-            for (int L = 0; L < NLIST; ++L) {
-                excl[L] = inc[L] - v[L];
-                int tot = __shfl_sync(FULL, inc[L], 31);
-                if (lane == 0) sm.scan_tot[L] = tot;
-            }
-            __syncwarp();
-        } else {
-#pragma unroll
-            for (int L = 0; L < NLIST; ++L)
-                if (lane == 31) bx.scan_w[L][warp] = inc[L];
-            sync();
-            if (warp == 0) {
-#pragma unroll
-                for (int L = 0; L < NLIST; ++L) {
-                    int x0 = lane < TS / 32 ? bx.scan_w[L][lane] : 0, x = x0;
-#pragma unroll
-                    for (int o = 1; o < 32; o <<= 1) {
-                        int y = __shfl_up_sync(FULL, x, o);
-                        if (lane >= o) x += y;
-                    }
-                    bx.scan_w[L][lane] = x - x0;
-                    if (lane == 31) sm.scan_tot[L] = x;
-                }
-            }
-            sync();
-#pragma unroll
-            for (int L = 0; L < NLIST; ++L) excl[L] = bx.scan_w[L][warp] + inc[L] - v[L];
-        }
-    }
-
     __device__ __forceinline__ void word_lists(const uint32_t *Rn, int g, int l, uint32_t (&m)[NLIST]) {
         uint32_t r = Rn[g], lf = mask(M_LEAF)[g];
         m[L_INT] = r & ~lf;
@@ -698,50 +652,66 @@ struct Worker {
         m[L_GH] = mask(M_GH)[g];
     }
 
+    // Rounds of TS consecutive mask words, one word per thread; a block scan of
+    // the per-word counts places each word's entries (the lists stay sorted by
+    // level, then cell).  A dense word costs its owner at most 32 stores per
+    // list, and dense levels are spread over as many threads as they have words.
     __device__ void build_lists(const uint32_t *Rn) {
-        int C = (d.Wtot + TS - 1) / TS;
-        int g0 = tid * C, g1 = min(d.Wtot, g0 + C);
-        int cnt[NLIST] = {0, 0, 0, 0, 0}, off[NLIST];
-        for (int g = g0; g < g1; ++g) {
-            int l, wi;
-            level_of_word(sm, g, l, wi);
-            uint32_t m[NLIST];
-            word_lists(Rn, g, l, m);
-#pragma unroll
-            for (int L = 0; L < NLIST; ++L) cnt[L] += __popc(m[L]);
-        }
-        team_scan(cnt, off);
-        tick(T_LISTS_COUNT);
-        for (int g = g0; g < g1; ++g) {
-            int l, wi;
-            level_of_word(sm, g, l, wi);
-            if (wi == 0)
-#pragma unroll
-                for (int L = 0; L < NLIST; ++L) sm.seg[L][l] = off[L];
-            uint32_t m[NLIST];
-            word_lists(Rn, g, l, m);
+        constexpr int NW = TS / 32;
+        const int lane = tid & 31, warp = tid >> 5;
+        const int Wtot = d.Wtot;
+        uint32_t *pr = mask(M_PRED), *gh = mask(M_GH);
+        int run[NLIST] = {0, 0, 0, 0, 0};
+        for (int r = 0, base = 0; base < Wtot; ++r, base += TS) {
+            const int g = base + tid;
+            const bool valid = g < Wtot;
+            int l = 0, wi = 0;
+            uint32_t m[NLIST] = {0u, 0u, 0u, 0u, 0u};
+            if (valid) {
+                level_of_word(sm, g, l, wi);
+                word_lists(Rn, g, l, m);
+                // consumed: as KEEP / REF these words must start the next step at zero
+                pr[g] = 0u;
+                gh[g] = 0u;
+            }
+            int inc[NLIST];
 #pragma unroll
             for (int L = 0; L < NLIST; ++L) {
-                uint32_t *dst = list(L);
-                uint32_t x = m[L];
-                while (x) {
-                    int bit = __ffs(x) - 1;
-                    x &= x - 1;
-                    dst[off[L]++] = pack(l, 32LL * wi + bit);
+                int x = __popc(m[L]);
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const int y = __shfl_up_sync(FULL, x, o);
+                    if (lane >= o) x += y;
                 }
+                inc[L] = x;
+            }
+            int(*sw)[32] = bx.scan_w[r & 1];  // alternate buffers: one barrier per round
+            if (lane == 31)
+#pragma unroll
+                for (int L = 0; L < NLIST; ++L) sw[L][warp] = inc[L];
+            sync();
+            const uint32_t pk = pack(l, 32LL * wi);
+#pragma unroll
+            for (int L = 0; L < NLIST; ++L) {
+                const int v = lane < NW ? sw[L][lane] : 0;
+                const int before = __reduce_add_sync(FULL, lane < warp ? v : 0);
+                const int tot = __reduce_add_sync(FULL, v);
+                uint32_t x = m[L];
+                int off = run[L] + before + inc[L] - __popc(x);
+                if (valid && wi == 0) sm.seg[L][l] = off;
+                uint32_t *dst = list(L);
+                while (x) {
+                    const int bit = __ffs(x) - 1;
+                    x &= x - 1u;
+                    dst[off++] = pk + (uint32_t)bit;
+                }
+                run[L] += tot;
             }
         }
-        sync();
         if (tid == 0) {
 #pragma unroll
-            for (int L = 0; L < NLIST; ++L) sm.seg[L][d.Jmax + 1] = sm.scan_tot[L];
-            sm.nleaf = sm.scan_tot[L_LEAF];
-        }
-        // the PRED / GH words are consumed: as KEEP / REF they must start the next step at zero
-        uint32_t *pr = mask(M_PRED), *gh = mask(M_GH);
-        for (int g = tid; g < d.Wtot; g += TS) {
-            pr[g] = 0u;
-            gh[g] = 0u;
+            for (int L = 0; L < NLIST; ++L) sm.seg[L][d.Jmax + 1] = run[L];
+            sm.nleaf = run[L_LEAF];
         }
         sync();
     }
