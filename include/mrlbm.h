@@ -161,6 +161,25 @@ mr_status mr_stats(mr_ctx *ctx, unsigned long long *updates, unsigned long long 
  * Takes effect at the next launch. */
 mr_status mr_set_launch(mr_ctx *ctx, int block, int grid);
 
+/* Order in which the persistent launch's work queue hands out the instances:
+ * by_fields = 1 (default) groups them by field count, largest first within a
+ * group; 0 orders by size (nf 2^Jmax) alone.  Stream-ordered. */
+mr_status mr_set_order(mr_ctx *ctx, int by_fields);
+
+/* Autotuner of the batch driver (the paper has no counterpart).  Times nsteps
+ * adaptive steps of the context's current state under each launch shape --
+ * threads per block 128, 256, 512, 1024 (the cells of a level each block
+ * sweeps per pass) times both queue orders of mr_set_order -- and keeps the
+ * fastest.  Before every trial, and once more at the end, the state is
+ * restored from scratch: caller-owned device memory of at least
+ * mr_workspace_size bytes, which receives a copy of the workspace.  The
+ * results are unchanged by the launch shape (every shape computes the same
+ * values), so the state after the call equals the state before it.
+ * Synchronises the stream; not for use during stream capture.  best_block,
+ * best_order and best_ms (the fastest trial in milliseconds) may be NULL. */
+mr_status mr_autotune(mr_ctx *ctx, int nsteps, void *scratch, size_t scratch_bytes, int *best_block,
+                      int *best_order, float *best_ms);
+
 /* Reconstruction coefficients used by the stream (Section 3.3 with gamma = 1):
  * for a leaf at level gap dj = Jmax - l (0 <= dj <= 24), kind 0 gives the
  * 4 weights of the first finest cell on the level-l window (k-2, k-1, k, k+1),

@@ -88,6 +88,34 @@ class MRLBM:
         """Threads per block (128, 256, 512 or 1024) and blocks (0: one resident wave)."""
         capi.check(self.h, self.lib.mr_set_launch(self.h, block, grid))
 
+    def set_order(self, by_fields: bool):
+        """Work-queue order: field count first (default) or size alone."""
+        capi.check(self.h, self.lib.mr_set_order(self.h, 1 if by_fields else 0))
+
+    def autotune(self, nsteps: int = 8) -> dict:
+        """Time nsteps steps under every launch shape (block size x queue order)
+        and keep the fastest; the state is restored, so results are unchanged."""
+        import torch
+
+        scratch = torch.empty(self.workspace_bytes, dtype=torch.uint8, device=self.device)
+        b, o, ms = ctypes.c_int(), ctypes.c_int(), ctypes.c_float()
+        capi.check(self.h, self.lib.mr_autotune(self.h, nsteps, ctypes.c_void_p(scratch.data_ptr()),
+                                                self.workspace_bytes, ctypes.byref(b), ctypes.byref(o),
+                                                ctypes.byref(ms)))
+        del scratch
+        return {"block": b.value, "order_by_fields": bool(o.value), "ms_per_trial": ms.value, "steps": nsteps}
+
+    def capture(self, nsteps: int):
+        """A CUDA graph holding one persistent launch of nsteps adaptive steps on
+        this context's stream; ``replay()`` advances every instance by nsteps."""
+        import torch
+
+        torch.cuda.synchronize(self.device)
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=self.stream):
+            capi.check(self.h, self.lib.mr_advance(self.h, nsteps))
+        return g
+
     # -- state -------------------------------------------------------------
     def initial_data(self) -> np.ndarray:
         return np.concatenate([np.ascontiguousarray(i.m0, dtype=np.float64).ravel() for i in self.instances])

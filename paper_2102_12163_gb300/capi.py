@@ -51,6 +51,8 @@ SIGNATURES = {
     "mr_get_summary": [_vp, _P(_d), _P(_i)],
     "mr_stats": [_vp, _P(ctypes.c_ulonglong), _P(ctypes.c_ulonglong), _P(ctypes.c_longlong)],
     "mr_set_launch": [_vp, _i, _i],
+    "mr_set_order": [_vp, _i],
+    "mr_autotune": [_vp, _i, _vp, ctypes.c_size_t, _P(_i), _P(_i), _P(ctypes.c_float)],
     "mr_reconstruction_coefficients": [_i, _i, _P(_d)],
     "mr_phase_times": [_vp, _i, _P(ctypes.c_ulonglong), _i],
     "mr_info": [_vp, _P(_i), _P(ctypes.c_longlong)],

@@ -58,7 +58,9 @@ struct mr_ctx {
     bool bound = false, initialised = false;
     int block = 0, grid = 0, grid_req = 0, sms = 0;
     int mask_cap = 0;    // words per bitmask a block team keeps in shared memory
+    int wmax = 0;        // mask words of the largest instance
     bool order_by_fields = true;
+    std::vector<int> order_host;  // staging of the queue order (kept alive for the async copy)
     long long launches = 0;
     std::string err;
 
@@ -341,6 +343,44 @@ mr_status mr_workspace_size(const mr_ctx *cc, size_t *bytes) {
     return MR_OK;
 }
 
+// Launch shape for the context's block size: shared-memory bitmasks of as many
+// words as the largest instance needs, within a per-block budget (a lone
+// instance may use most of the SM; a batch keeps several blocks resident), and
+// one wave of resident blocks unless the caller fixed the grid.
+static int configure(mr_ctx *c) {
+    // resident blocks the registers allow (64 per thread) share the SM's 227 KB
+    int by_regs = std::max(1, 65536 / (c->block * 64));
+    size_t budget = c->n() == 1 ? 220u * 1024u : (227u * 1024u) / (size_t)by_regs - 1024u;
+    size_t base = mrg_smem_bytes(c->fp32(), c->block, 0);
+    int fit = budget > base ? (int)((budget - base) / (NMASK * sizeof(uint32_t))) : 0;
+    c->mask_cap = std::min(c->wmax, fit);
+    int nb = 0;
+    int rc = c->cuda((cudaError_t)mrg_occupancy(c->fp32(), c->block, c->mask_cap, &nb), "occupancy");
+    if (rc) return rc;
+    c->grid = c->grid_req > 0 ? c->grid_req : std::max(1, nb) * c->sms;
+    return MR_OK;
+}
+
+// Processing order of the work queue: by field count first (blocks resident
+// together then run the same scheme's code, which keeps the instruction cache
+// warm) unless disabled, then largest first (nf 2^Jmax as the cost estimate).
+static int upload_order(mr_ctx *c) {
+    const int n = c->n();
+    const std::vector<InstDesc> &dd = c->hdesc;
+    std::vector<int> order(n);
+    for (int i = 0; i < n; ++i) order[i] = i;
+    std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
+        if (c->order_by_fields && dd[x].nf != dd[y].nf) return dd[x].nf > dd[y].nf;
+        double cx = (double)dd[x].nf * std::ldexp(1.0, dd[x].Jmax);
+        double cy = (double)dd[y].nf * std::ldexp(1.0, dd[y].Jmax);
+        return cx > cy;
+    });
+    c->order_host = order;
+    return c->cuda(cudaMemcpyAsync(c->ws + c->off_order, c->order_host.data(), sizeof(int) * n, cudaMemcpyHostToDevice,
+                                   c->stream),
+                   "upload");
+}
+
 mr_status mr_bind(mr_ctx *c, void *ws, size_t bytes, void *stream) {
     if (!c || !ws) return MR_ERR_ARG;
     size_t need = 0;
@@ -372,17 +412,6 @@ mr_status mr_bind(mr_ctx *c, void *ws, size_t bytes, void *stream) {
         c->block = n == 1 ? (jmax >= 12 ? 1024 : 512) : 256;
     }
     c->hdesc = dd;
-    // processing order: by field count (blocks resident together then run the
-    // same scheme's code, which keeps the instruction cache warm), then largest
-    // first (nf 2^Jmax as the cost estimate)
-    std::vector<int> order(n), ident(n);
-    for (int i = 0; i < n; ++i) order[i] = ident[i] = i;
-    std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
-        if (c->order_by_fields && dd[x].nf != dd[y].nf) return dd[x].nf > dd[y].nf;
-        double cx = (double)dd[x].nf * std::ldexp(1.0, dd[x].Jmax);
-        double cy = (double)dd[y].nf * std::ldexp(1.0, dd[y].Jmax);
-        return cx > cy;
-    });
     Tables<double> td;
     Tables<float> tf;
     make_tables(td, tf);
@@ -390,29 +419,18 @@ mr_status mr_bind(mr_ctx *c, void *ws, size_t bytes, void *stream) {
     if ((rc = c->cuda(cudaMemcpyAsync(c->ws + c->off_desc, dd.data(), sizeof(InstDesc) * n, cudaMemcpyHostToDevice, s), "upload")))
         return (mr_status)rc;
     if ((rc = c->cuda(cudaMemsetAsync(c->ws + c->off_state, 0, sizeof(InstState) * n, s), "memset"))) return (mr_status)rc;
-    if ((rc = c->cuda(cudaMemcpyAsync(c->ws + c->off_order, order.data(), sizeof(int) * n, cudaMemcpyHostToDevice, s), "upload")))
-        return (mr_status)rc;
+    if ((rc = upload_order(c))) return (mr_status)rc;
+    std::vector<int> ident(n);
+    for (int i = 0; i < n; ++i) ident[i] = i;
     if ((rc = c->cuda(cudaMemcpyAsync(c->ws + c->off_ident, ident.data(), sizeof(int) * n, cudaMemcpyHostToDevice, s), "upload")))
         return (mr_status)rc;
     if ((rc = c->cuda(cudaMemcpyAsync(c->ws + c->off_tab, &td, sizeof td, cudaMemcpyHostToDevice, s), "upload"))) return (mr_status)rc;
     if ((rc = c->cuda(cudaMemcpyAsync(c->ws + c->off_tab + sizeof td, &tf, sizeof tf, cudaMemcpyHostToDevice, s), "upload")))
         return (mr_status)rc;
     if ((rc = c->cuda(cudaStreamSynchronize(s), "cudaStreamSynchronize"))) return (mr_status)rc;
-    // shared-memory bitmasks: as many words as the largest instance needs,
-    // within a per-block budget (a lone instance may use most of the SM; a
-    // batch keeps several blocks resident)
-    int wmax = 0;
-    for (int i = 0; i < n; ++i) wmax = std::max(wmax, dd[i].Wtot);
-    // resident blocks the registers allow (64 per thread) share the SM's 227 KB
-    int by_regs = std::max(1, 65536 / (c->block * 64));
-    size_t budget = n == 1 ? 220u * 1024u : (227u * 1024u) / (size_t)by_regs - 1024u;
-    size_t base = mrg_smem_bytes(c->fp32(), c->block, 0);
-    int fit = budget > base ? (int)((budget - base) / (NMASK * sizeof(uint32_t))) : 0;
-    c->mask_cap = std::min(wmax, fit);
-    int nb = 0;
-    if ((rc = c->cuda((cudaError_t)mrg_occupancy(c->fp32(), c->block, c->mask_cap, &nb), "occupancy")))
-        return (mr_status)rc;
-    c->grid = c->grid_req > 0 ? c->grid_req : std::max(1, nb) * c->sms;
+    c->wmax = 0;
+    for (int i = 0; i < n; ++i) c->wmax = std::max(c->wmax, dd[i].Wtot);
+    if ((rc = configure(c))) return (mr_status)rc;
     c->bound = true;
     c->initialised = false;
     return MR_OK;
@@ -668,18 +686,74 @@ mr_status mr_set_launch(mr_ctx *c, int block, int grid) {
     if (grid < 0) return (mr_status)c->fail(MR_ERR_ARG, "grid must be >= 0");
     c->block = block;
     c->grid_req = grid;
-    if (c->bound) {
-        // keep the shared-memory request of the new block size within its share of the SM
-        int by_regs = std::max(1, 65536 / (c->block * 64));
-        size_t base = mrg_smem_bytes(c->fp32(), c->block, 0);
-        size_t limit = c->n() == 1 ? 220u * 1024u : (227u * 1024u) / (size_t)by_regs - 1024u;
-        int fit = limit > base ? (int)((limit - base) / (NMASK * sizeof(uint32_t))) : 0;
-        c->mask_cap = std::min(c->mask_cap, fit);
-        int nb = 0;
-        int rc = c->cuda((cudaError_t)mrg_occupancy(c->fp32(), c->block, c->mask_cap, &nb), "occupancy");
-        if (rc) return (mr_status)rc;
-        c->grid = grid > 0 ? grid : std::max(1, nb) * c->sms;
+    if (c->bound) return (mr_status)configure(c);
+    return MR_OK;
+}
+
+mr_status mr_set_order(mr_ctx *c, int by_fields) {
+    if (!c || (by_fields != 0 && by_fields != 1)) return MR_ERR_ARG;
+    c->order_by_fields = by_fields != 0;
+    if (c->bound) return (mr_status)upload_order(c);
+    return MR_OK;
+}
+
+mr_status mr_autotune(mr_ctx *c, int nsteps, void *scratch, size_t scratch_bytes, int *best_block, int *best_order,
+                      float *best_ms) {
+    if (!c || nsteps < 1 || !scratch) return MR_ERR_ARG;
+    if (!c->initialised) return (mr_status)c->fail(MR_ERR_STATE, "mr_autotune needs an initial state");
+    if (scratch_bytes < c->total)
+        return (mr_status)c->fail(MR_ERR_CAPACITY, "autotune scratch of %zu bytes, need %zu", scratch_bytes, c->total);
+    cudaStream_t s = c->stream;
+    int rc = c->cuda(cudaMemcpyAsync(scratch, c->ws, c->total, cudaMemcpyDeviceToDevice, s), "save state");
+    if (rc) return (mr_status)rc;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if ((rc = c->cuda(cudaEventCreate(&e0), "cudaEventCreate"))) return (mr_status)rc;
+    if ((rc = c->cuda(cudaEventCreate(&e1), "cudaEventCreate"))) {
+        cudaEventDestroy(e0);
+        return (mr_status)rc;
     }
+    const int blocks[4] = {128, 256, 512, 1024};
+    const int norders = c->n() > 1 ? 2 : 1;
+    const int block0 = c->block, grid0 = c->grid_req;
+    const bool order0 = c->order_by_fields;
+    int bb = block0, bo = order0 ? 1 : 0;
+    float bt = -1.0f;
+    auto restore = [&]() { return c->cuda(cudaMemcpyAsync(c->ws, scratch, c->total, cudaMemcpyDeviceToDevice, s), "restore"); };
+    for (int ib = 0; ib < 4 && !rc; ++ib)
+        for (int io = 0; io < norders && !rc; ++io) {
+            c->block = blocks[ib];
+            c->grid_req = 0;
+            c->order_by_fields = norders == 1 ? order0 : io == 0;
+            if ((rc = configure(c)) || (rc = upload_order(c))) break;
+            // untimed step first (first launch of a block size sets its attributes), then the trial
+            if ((rc = restore()) || (rc = launch(c, PH_ADAPT | PH_STEP, 1, -1, nullptr, nullptr)) || (rc = restore())) break;
+            if ((rc = c->cuda(cudaEventRecord(e0, s), "cudaEventRecord"))) break;
+            if ((rc = launch(c, PH_ADAPT | PH_STEP, nsteps, -1, nullptr, nullptr))) break;
+            if ((rc = c->cuda(cudaEventRecord(e1, s), "cudaEventRecord"))) break;
+            if ((rc = c->cuda(cudaEventSynchronize(e1), "cudaEventSynchronize"))) break;
+            float ms = 0.0f;
+            if ((rc = c->cuda(cudaEventElapsedTime(&ms, e0, e1), "cudaEventElapsedTime"))) break;
+            if (bt < 0.0f || ms < bt) {
+                bt = ms;
+                bb = c->block;
+                bo = c->order_by_fields ? 1 : 0;
+            }
+        }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    // the fastest shape (the caller's on failure) and the saved state
+    c->block = rc ? block0 : bb;
+    c->grid_req = rc ? grid0 : 0;
+    c->order_by_fields = rc ? order0 : bo != 0;
+    int rc2 = configure(c);
+    if (!rc2) rc2 = upload_order(c);
+    if (!rc2) rc2 = restore();
+    if (!rc2) rc2 = c->cuda(cudaStreamSynchronize(s), "cudaStreamSynchronize");
+    if (rc) return (mr_status)rc;
+    if (rc2) return (mr_status)rc2;
+    if (best_block) *best_block = bb;
+    if (best_order) *best_order = bo;
+    if (best_ms) *best_ms = bt;
     return MR_OK;
 }
 

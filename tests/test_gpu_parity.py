@@ -289,3 +289,37 @@ def test_nonfinite_populations_are_reported():
     with pytest.raises(MRError) as ei:
         s.sync()
     assert ei.value.code == -4
+
+
+def test_autotune_leaves_the_state_and_results_unchanged():
+    insts = W.batch(n=24, seed=31, Jmax_range=(6, 11))
+    a, b = _solver(insts), _solver(insts)
+    a.advance(3)
+    b.advance(3)
+    tune = a.autotune(2)
+    assert tune["block"] in (128, 256, 512, 1024) and tune["ms_per_trial"] > 0.0
+    assert a.stats()[0] == b.stats()[0]  # counters restored with the state
+    a.advance(5)
+    b.advance(5)
+    for i in range(len(insts)):
+        assert np.array_equal(a.tree(i), b.tree(i)), i
+        assert np.array_equal(a.leaves(i)[2], b.leaves(i)[2]), i
+    assert a.stats() == b.stats()
+
+
+def test_graph_replay_equals_advance():
+    import torch
+
+    insts = W.batch(n=16, seed=32, Jmax_range=(6, 10))
+    a, b = _solver(insts, precision=MR_FP32_MIXED), _solver(insts, precision=MR_FP32_MIXED)
+    g = a.capture(4)
+    with torch.cuda.stream(a.stream):
+        for _ in range(3):
+            g.replay()
+    b.advance(12)
+    a.sync()
+    b.sync()
+    for i in range(len(insts)):
+        assert np.array_equal(a.tree(i), b.tree(i)), i
+        assert np.array_equal(a.leaves(i)[2], b.leaves(i)[2]), i
+    assert a.stats() == b.stats()
