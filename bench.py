@@ -316,6 +316,42 @@ def accuracy(insts, steps: int, every: int = 256):
     }
 
 
+def accuracy_scalar(inst, name: str):
+    """Tests I-IV of Table 1 at their final time: E = reference scheme (the FP64
+    path at eps = 0) against the exact solution, delta = adaptive against the
+    reference, for both precisions, with the paper's Table 2 ratio at s = 1."""
+    import numpy as np
+
+    from paper_2102_12163_gb300 import MR_FP32_MIXED, MR_FP64, MRLBM
+    from paper_2102_12163_gb300 import workloads as W
+
+    test = {"test1": "I", "test2": "II", "test3": "III", "test4": "IV"}[name]
+    table2_s1 = {"I": 59.4, "II": 2310.0, "III": 37.1, "IV": 341.0}[test]
+    N = inst.nsteps
+
+    def run(prec, eps):
+        i = inst.with_(eps=eps)
+        s = MRLBM(i, precision=prec)
+        s.set_initial()
+        s.advance(N)
+        s.sync()
+        out, nl = s.finest()[0], len(s.leaves()[0])
+        s.close()
+        return out, nl
+
+    M, _ = run(MR_FP64, 0.0)
+    exact = W.scalar_exact(test, W.cell_edges(inst.a, inst.b, inst.Jmax), N * inst.dx / inst.lam)
+    E = float(inst.dx * np.abs(exact - M).sum())
+    out = {"test": test, "s": inst.s[0], "steps": N, "E_reference_vs_exact": E,
+           "table2_E_over_delta_at_s1": table2_s1}
+    for key, prec in (("fp64", MR_FP64), ("fp32", MR_FP32_MIXED)):
+        f, nl = run(prec, inst.eps)
+        d = float(inst.dx * np.abs(M - f).sum())
+        out[key] = {"delta": d, "E_over_delta": E / d if d > 0 else None,
+                    "compression_percent": 100.0 * (1.0 - nl / (1 << inst.Jmax))}
+    return out
+
+
 # --------------------------------------------------------------------------- main
 
 def main():
@@ -325,7 +361,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=16)
     ap.add_argument("--instances", type=int, default=4096, help="batch size (smaller only for profiling)")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="batch", choices=["batch", "advection", "burgers", "shallow", "sod"])
+    ap.add_argument("--workload", default="batch",
+                    choices=["batch", "advection", "burgers", "shallow", "sod", "test1", "test2", "test3", "test4"])
     ap.add_argument("--block", type=int, default=None)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true", help="same as --precision fp32")
@@ -383,6 +420,8 @@ def main():
     acc = None
     if rank == 0 and not args.no_accuracy and args.workload == "batch":
         acc = accuracy(insts, min(args.steps, 64))
+    elif rank == 0 and not args.no_accuracy and args.workload.startswith("test"):
+        acc = accuracy_scalar(insts[0], args.workload)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

@@ -1,9 +1,10 @@
 """Seeded synthetic workloads shaped like the test cases of arXiv 2102.12163.
 
-This module only describes problems: parameters and the exact cell averages of
-the initial conserved moments on the finest lattice.  It holds none of the
-method's arithmetic, and both the CUDA path and the CPU oracle take their
-inputs from it.
+This module only describes problems: parameters, the exact cell averages of
+the initial conserved moments on the finest lattice and, for the scalar test
+cases of Table 1, the cell averages of the exact entropy solution of the PDE
+at a later time.  It holds none of the method's arithmetic, and both the CUDA
+path and the CPU oracle take their inputs from it.
 
 Workloads (Section 5 of the paper for the shapes; the paper's own runs use
 Jmax = 9 and unstated boundary conditions):
@@ -18,6 +19,9 @@ Jmax = 9 and unstated boundary conditions):
   batch      4096 seeded instances mixing the four families, Jmax in 8..14,
              eps log-uniform in [1e-5, 1e-2], piecewise-constant data with
              1..6 jumps, periodic.
+  test1..4   the scalar D1Q2 test cases I-IV of Table 1 (Section 5.1):
+             Omega = [-3, 3], lambda = 1, Jmin 2, Jmax 9, gamma 1, eps 1e-4,
+             with their exact solutions (scalar_test, scalar_exact).
 """
 from __future__ import annotations
 
@@ -217,9 +221,97 @@ def random_smooth(Jmax: int, eq: int, seed: int, Jmin: int = 2, eps: float = 1e-
     return inst
 
 
+# the scalar test cases of Table 1 (Section 5.1) ------------------------------
+
+def _logcosh(y):
+    a = np.abs(y)
+    return a + np.log1p(np.exp(-2.0 * a)) - math.log(2.0)
+
+
+def _tanh_prim(x):
+    """Primitive of (1 + tanh(100 x)) / 2."""
+    return 0.5 * (x + _logcosh(100.0 * x) / 100.0)
+
+
+def _tanh_profile(x):
+    return 0.5 * (1.0 + np.tanh(100.0 * x))
+
+
+def _gauss_prim(x):
+    """Primitive of exp(-20 x^2)."""
+    from scipy.special import erf
+
+    return math.sqrt(math.pi / 20.0) / 2.0 * erf(math.sqrt(20.0) * x)
+
+
+# Test -> (equation, final time T, regularity nu of Table 1 as mu_bar (reading:
+# mu_bar = min(nu, 2 gamma + 1)), boundary condition)
+SCALAR_TESTS = {
+    "I": (EQ_ADVECTION, 0.4, 3, BC_PERIODIC),
+    "II": (EQ_ADVECTION, 0.4, 0, BC_PERIODIC),
+    "III": (EQ_BURGERS, 0.4, 3, BC_COPY),
+    "IV": (EQ_BURGERS, 0.7, 0, BC_PERIODIC),
+}
+
+
+def scalar_test(test: str, s: float = 1.0, Jmax: int = 9, eps: float = 1e-4, Jmin: int = 2) -> Instance:
+    """Test I-IV of Table 1: advection (c = 3/4) of exp(-20 x^2) and of the
+    indicator of |x| <= 1/2, Burgers with (1 + tanh(100 x)) / 2 and with the
+    indicator of |x| <= 1/2; Omega = [-3, 3], lambda = 1, relaxation s."""
+    eq, T, mu_bar, bc = SCALAR_TESTS[test]
+    inst = Instance(f"test{test}", eq, Jmin, Jmax, eps, 1.0, -3.0, 3.0, bc, T, mu_bar=mu_bar, s=(s,),
+                    eqp=0.75 if eq == EQ_ADVECTION else 0.0)
+    inst.m0 = scalar_exact(test, cell_edges(inst.a, inst.b, Jmax), 0.0)[None, :]
+    return inst
+
+
+def scalar_exact(test: str, edges: np.ndarray, t: float) -> np.ndarray:
+    """Cell averages over the cells [edges[i], edges[i+1]] of the exact entropy
+    solution of Test I-IV at time t (no wave reaches the boundary before T)."""
+    x = np.asarray(edges, dtype=np.float64)
+    dx = np.diff(x)
+    if test == "I":  # advection at c = 3/4
+        return np.diff(_gauss_prim(x - 0.75 * t)) / dx
+    if test == "II":
+        return avg_indicator(x, -0.5 + 0.75 * t, 0.5 + 0.75 * t)
+    if test == "III":
+        # smooth increasing datum: rho(t, x) = rho0(xi) with x = xi + t rho0(xi); in the
+        # variable xi, int rho dx = int rho0 (1 + t rho0') dxi = [P0(xi) + t rho0(xi)^2 / 2]
+        if t == 0.0:
+            return np.diff(_tanh_prim(x)) / dx
+        lo, hi = x - t, x.copy()  # xi + t rho0(xi) is increasing, rho0 in (0, 1)
+        for _ in range(200):
+            mid = 0.5 * (lo + hi)
+            f = mid + t * _tanh_profile(mid) - x
+            lo = np.where(f < 0.0, mid, lo)
+            hi = np.where(f < 0.0, hi, mid)
+        xi = 0.5 * (lo + hi)
+        G = _tanh_prim(xi) + 0.5 * t * _tanh_profile(xi) ** 2
+        return np.diff(G) / dx
+    if test == "IV":
+        # rarefaction from x = -1/2 (head -1/2 + t), shock from x = 1/2 at speed 1/2 (t < 2)
+        if t == 0.0:
+            return avg_indicator(x, -0.5, 0.5)
+        a, b = x[:-1], x[1:]
+
+        def fan(u):  # primitive of (u + 1/2) / t
+            return (u + 0.5) ** 2 / (2.0 * t)
+
+        r0, r1 = -0.5, -0.5 + t
+        lo_f, hi_f = np.clip(a, r0, r1), np.clip(b, r0, r1)
+        out = fan(hi_f) - fan(lo_f)
+        out += np.clip(np.minimum(b, 0.5 + 0.5 * t) - np.maximum(a, r1), 0.0, None)
+        return out / dx
+    raise ValueError(test)
+
+
 WORKLOADS = {
     "advection": advection,
     "burgers": burgers,
     "shallow": shallow_water,
     "sod": sod,
+    "test1": lambda: scalar_test("I"),
+    "test2": lambda: scalar_test("II"),
+    "test3": lambda: scalar_test("III"),
+    "test4": lambda: scalar_test("IV"),
 }

@@ -67,6 +67,9 @@ PARITY_CASES = [
     ("euler-periodic-J10", lambda: W.random_smooth(10, W.EQ_EULER, seed=4, eps=3e-4)),
     ("euler-copy-J11-jmin4", lambda: W.random_smooth(11, W.EQ_EULER, seed=5, eps=1e-4, bc=W.BC_COPY, Jmin=4)),
     ("adv-config", lambda: W.advection()),
+    ("testI-s1.75", lambda: W.scalar_test("I", s=1.75)),
+    ("testIII-copy", lambda: W.scalar_test("III", s=1.25)),
+    ("testIV", lambda: W.scalar_test("IV", s=0.75)),
 ]
 
 
@@ -323,3 +326,30 @@ def test_graph_replay_equals_advance():
         assert np.array_equal(a.tree(i), b.tree(i)), i
         assert np.array_equal(a.leaves(i)[2], b.leaves(i)[2]), i
     assert a.stats() == b.stats()
+
+
+@pytest.mark.parametrize("test", ["I", "II", "III", "IV"])
+def test_scalar_tests_full_run_errors(test):
+    """Tests I-IV of Table 1 run to their final time on the GPU: the FP64 path's
+    trajectory and delta equal the oracle's, and in both precisions delta stays
+    far below the reference scheme's error E against the exact solution."""
+    inst = W.scalar_test(test, s=1.0)
+    N = inst.nsteps
+    ref = _solver(inst.with_(eps=0.0))
+    ref.advance(N)
+    M = ref.finest()[0]
+    exact = W.scalar_exact(test, W.cell_edges(inst.a, inst.b, inst.Jmax), N * inst.dx / inst.lam)
+    E = inst.dx * np.abs(exact - M).sum()
+    o = oracle_of(inst)
+    o.step(N)
+    d_oracle = inst.dx * np.abs(M - o.finest_moments()[0]).sum()
+    for prec in (MR_FP64, MR_FP32_MIXED):
+        s = _solver(inst, precision=prec)
+        s.advance(N)
+        d = inst.dx * np.abs(M - s.finest()[0]).sum()
+        if prec == MR_FP64:
+            R, _, lvs = gpu_state(s)
+            assert np.array_equal(R, o.get_state()[0])
+            assert_same_leaves(lvs, o, tol=1e-11)
+            assert abs(d - d_oracle) <= 1e-10
+        assert E / d > 5.0, (test, prec, E, d)

@@ -2,7 +2,6 @@
 (Sections 2, 4 and 5)."""
 import numpy as np
 import pytest
-from scipy.special import erf
 
 import oracle as O
 from conftest import read_golden
@@ -180,19 +179,11 @@ def test_threshold_on_a_dyadic_step():
         assert np.array_equal(Tl[l].astype(bool), expect >= eps_l)
 
 
-def _advection_test(test, s, mu_bar, J=9, eps=1e-4):
-    a, b = -3.0, 3.0
-    e = W.cell_edges(a, b, J)
-    c = 0.75
-    inst = W.Instance("t", W.EQ_ADVECTION, 2, J, eps, 1.0, a, b, W.BC_PERIODIC, 0.4, s=(s,), eqp=c, mu_bar=mu_bar)
-    if test == "I":
-        prim = lambda x: np.sqrt(np.pi / 20) / 2 * erf(np.sqrt(20) * x)  # noqa: E731
-        avg = lambda x: np.diff(prim(x)) / np.diff(x)  # noqa: E731
-        inst.m0 = avg(e)[None, :]
-        exact = lambda t: avg(e - c * t)  # noqa: E731
-    else:
-        inst.m0 = W.avg_indicator(e, -0.5, 0.5)[None, :]
-        exact = lambda t: W.avg_indicator(e, -0.5 + c * t, 0.5 + c * t)  # noqa: E731
+def _scalar_errors(test, s, J=9, eps=1e-4):
+    """Test I-IV of Table 1: E = reference scheme vs exact solution, delta =
+    adaptive vs reference scheme (weighted l1 of the conserved moment at the
+    final step), and the compression factor CR."""
+    inst = W.scalar_test(test, s=s, Jmax=J, eps=eps)
     p = params_of(inst)
     o = O.Oracle(p)
     o.set_initial(inst.m0)
@@ -203,7 +194,8 @@ def _advection_test(test, s, mu_bar, J=9, eps=1e-4):
         F = O.uniform_step(p, F)
     M = O.moments(p, F)[0]
     dx = inst.dx
-    E = dx * np.abs(exact(N * dx / inst.lam) - M).sum()
+    exact = W.scalar_exact(test, W.cell_edges(inst.a, inst.b, J), N * dx / inst.lam)
+    E = dx * np.abs(exact - M).sum()
     delta = dx * np.abs(M - o.finest_moments()[0]).sum()
     cr = 100.0 * (1.0 - len(o.leaves()[0]) / (1 << J))
     return E, delta, cr, N
@@ -217,12 +209,61 @@ def test_table2_error_ratios_order_of_magnitude():
     not given, so only the order of magnitude is checked."""
     rows = {float(r[0]): [float(x) for x in r[1:]] for r in read_golden("table2_error_ratios.txt")}
     for s in (0.75, 1.0, 1.75):
-        E, d, cr, _ = _advection_test("I", s, 3)
+        E, d, cr, _ = _scalar_errors("I", s)
         assert rows[s][0] / 3 < E / d < rows[s][0] * 30, (s, E / d)
         assert cr > 70.0
-        E, d, cr, _ = _advection_test("II", s, 0)
+        E, d, cr, _ = _scalar_errors("II", s)
         assert rows[s][1] / 3 < E / d < rows[s][1] * 30, (s, E / d)
         assert cr > 70.0
+
+
+def test_burgers_tests_delta_is_far_below_the_discretisation_error():
+    """Tests III and IV (Burgers) at eps = 1e-4, Jmax = 9: the paper fixes
+    delta << E for every test (Section 5, choice of eps) and prints E / delta
+    in Table 2.  Our delta is never more than 3x the paper's (E / delta at
+    least a third of the printed ratio); it is often much smaller (more cells
+    are kept), so only this side is checked."""
+    rows = {float(r[0]): [float(x) for x in r[1:]] for r in read_golden("table2_error_ratios.txt")}
+    for s in (0.75, 1.0, 1.25, 1.5, 1.75):
+        for col, test in ((2, "III"), (3, "IV")):
+            E, d, cr, _ = _scalar_errors(test, s)
+            assert E / d > 5.0, (test, s, E / d)
+            assert E / d > rows[s][col] / 3, (test, s, E / d, rows[s][col])
+            assert cr > 60.0
+
+
+@pytest.mark.parametrize("test", ["I", "III", "IV"])
+def test_reference_scheme_converges_to_the_exact_solutions(test):
+    """Pin of the exact solutions of Tests I, III, IV (cell averages of the
+    entropy solution): the uniform reference scheme, first order, converges
+    to them as the lattice is refined (a wrong exact solution would leave an
+    O(1) error that does not shrink)."""
+    Es = []
+    for J in (9, 10, 11):
+        inst = W.scalar_test(test, Jmax=J)
+        p = params_of(inst)
+        F = O.equilibrium(p, inst.m0)
+        for _ in range(inst.nsteps):
+            F = O.uniform_step(p, F)
+        exact = W.scalar_exact(test, W.cell_edges(inst.a, inst.b, J), inst.nsteps * inst.dx / inst.lam)
+        Es.append(inst.dx * np.abs(exact - O.moments(p, F)[0]).sum())
+    assert Es[1] < 0.8 * Es[0] and Es[2] < 0.8 * Es[1], Es
+
+
+def test_exact_burgers_solutions_conserve_mass_up_to_the_boundary_flux():
+    """Test III (copy boundary): the total changes by the outflow phi(1) t = t / 2
+    through x = 3; Test IV: the total is conserved; the shock of Test IV sits
+    at x = 1/2 + t/2 (Rankine-Hugoniot speed (1 + 0) / 2)."""
+    e = W.cell_edges(-3.0, 3.0, 12)
+    dx = 6.0 / 4096
+    for t in (0.1, 0.4):
+        m0 = W.scalar_exact("III", e, 0.0).sum() * dx
+        assert abs(W.scalar_exact("III", e, t).sum() * dx - (m0 - 0.5 * t)) < 1e-9
+        assert abs(W.scalar_exact("IV", e, t).sum() * dx - 1.0) < 1e-12
+        m = W.scalar_exact("IV", e, t)
+        xs = 0.5 + 0.5 * t
+        i = int((xs + 3.0) / dx)
+        assert m[i - 2] == pytest.approx(1.0) and m[i + 2] == 0.0
 
 
 def test_perturbation_error_is_linear_in_eps():
@@ -232,7 +273,7 @@ def test_perturbation_error_is_linear_in_eps():
     epss = [1e-2, 1e-3, 1e-4, 1e-5]
     ds = []
     for eps in epss:
-        E, d, cr, N = _advection_test("II", 1.0, 0, J=9, eps=eps)
+        E, d, cr, N = _scalar_errors("II", 1.0, J=9, eps=eps)
         ds.append(d)
         assert d <= 10.0 * eps * (N + 1)
     slope = np.polyfit(np.log10(epss), np.log10(ds), 1)[0]
