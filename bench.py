@@ -364,6 +364,8 @@ def main():
     ap.add_argument("--workload", default="batch",
                     choices=["batch", "advection", "burgers", "shallow", "sod", "test1", "test2", "test3", "test4"])
     ap.add_argument("--block", type=int, default=None)
+    ap.add_argument("--gamma", type=int, default=1, choices=[1, 2, 3],
+                    help="prediction stencil half-width of every instance (Section 3.1)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true", help="same as --precision fp32")
     ap.add_argument("--precision", default="both", choices=["both", "fp32", "fp64"],
@@ -375,6 +377,12 @@ def main():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     insts, desc = make_workload(args.workload, rank, args.instances)
+    if args.gamma != 1:
+        for i in range(len(insts)):
+            m0 = insts[i].m0
+            insts[i] = insts[i].with_(gamma=args.gamma)
+            insts[i].m0 = m0
+        desc += f"; prediction stencil gamma = {args.gamma}"
     hbm, hbm_src = peaks()
 
     if args.impl == "reference":

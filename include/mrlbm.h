@@ -28,7 +28,9 @@
  *   - The library is not thread-safe per context.
  *
  * Scope of this build: D = 1, vectorial D1Q2^n schemes (velocities +-lambda per
- * field), prediction stencil gamma = 1 (c1 = -1/8), enlargement width sigma = 1.
+ * field), prediction stencils gamma = 1, 2, 3 (Section 3.1: c1 = -1/8; c1 =
+ * -22/128, c2 = 3/128; c1 = -201/1024, c2 = 11/256, c3 = -5/1024), enlargement
+ * width sigma = 1.
  */
 #ifndef MRLBM_H
 #define MRLBM_H
@@ -63,7 +65,7 @@ typedef enum { MR_EQ_ADVECTION = 0, MR_EQ_BURGERS = 1, MR_EQ_SW_VEC = 2, MR_EQ_E
 /* Per-instance description for the batched interface. */
 typedef struct {
     int Jmin, Jmax;   /* 2 <= Jmin <= Jmax <= 24 */
-    int gamma;        /* prediction stencil, must be 1 */
+    int gamma;        /* prediction stencil half-width: 1, 2 or 3 */
     int mu_bar;       /* Harten regularity guess, >= 0 (eq. HartenLossOfRegularity) */
     int bc;           /* mr_bc */
     int eq;           /* mr_equilibrium */
@@ -111,7 +113,7 @@ mr_status mr_set_initial(mr_ctx *ctx, const double *m_cons, size_t count);
  * cells numbered level by level (level l: [2^l - 2^Jmin, 2^(l+1) - 2^Jmin)),
  * S = 2^(Jmax+1) - 2^Jmin.  Only leaf values are used.  Device pointers.
  * The tree is checked on the host first (coarsest level whole, siblings
- * together, graded for gamma = 1); MR_ERR_ARG if it is not. */
+ * together, graded for the instance's gamma); MR_ERR_ARG if it is not. */
 mr_status mr_set_state(mr_ctx *ctx, int inst, const unsigned char *R, const double *values);
 
 /* ---- the adaptive step ------------------------------------------------ */

@@ -59,6 +59,7 @@ struct mr_ctx {
     int block = 0, grid = 0, grid_req = 0, sms = 0;
     int mask_cap = 0;    // words per bitmask a block team keeps in shared memory
     int wmax = 0;        // mask words of the largest instance
+    int n_narrow = 0;    // instances with gamma = 1 (first in the queue order)
     bool order_by_fields = true;
     std::vector<int> order_host;  // staging of the queue order (kept alive for the async copy)
     long long launches = 0;
@@ -88,7 +89,7 @@ struct mr_ctx {
 static int check_desc(mr_ctx *c, const mr_instance_desc &d, int i) {
     if (d.Jmin < 2 || d.Jmax < d.Jmin || d.Jmax > MAXLEV)
         return c->fail(MR_ERR_ARG, "instance %d: need 2 <= Jmin <= Jmax <= %d (got %d, %d)", i, MAXLEV, d.Jmin, d.Jmax);
-    if (d.gamma != 1) return c->fail(MR_ERR_ARG, "instance %d: only the gamma = 1 prediction is built", i);
+    if (d.gamma < 1 || d.gamma > 3) return c->fail(MR_ERR_ARG, "instance %d: gamma must be 1, 2 or 3", i);
     if (d.mu_bar < 0 || d.mu_bar > 30) return c->fail(MR_ERR_ARG, "instance %d: mu_bar out of range", i);
     if (d.bc != MR_BC_PERIODIC && d.bc != MR_BC_COPY) return c->fail(MR_ERR_ARG, "instance %d: bad boundary", i);
     if (nfields_of(d.eq) == 0) return c->fail(MR_ERR_ARG, "instance %d: bad equilibrium", i);
@@ -138,6 +139,7 @@ static void layout(mr_ctx *c) {
         h.eq = d.eq;
         h.nf = nf;
         h.mu_bar = d.mu_bar;
+        h.gamma = d.gamma;
         h.Wtot = W;
         h.eps = d.eps;
         h.a = d.a;
@@ -204,19 +206,26 @@ static void make_tables(Tables<double> &td, Tables<float> &tf) {
         }
         for (int j = 0; j < 2; ++j) tf.bf[dj][j] = (float)td.bf[dj][j];
     }
+    // prediction coefficients c_1..c_gamma (Section 3.1; gamma = 3 with c_3 = -5/1024,
+    // the sign that makes the stencil exact on polynomials of degree 5); all dyadic
+    const double pc[4][3] = {{0.0, 0.0, 0.0},
+                             {-1.0 / 8.0, 0.0, 0.0},
+                             {-22.0 / 128.0, 3.0 / 128.0, 0.0},
+                             {-201.0 / 1024.0, 11.0 / 256.0, -5.0 / 1024.0}};
+    for (int g = 0; g < 4; ++g)
+        for (int j = 0; j < 3; ++j) {
+            td.pc[g][j] = pc[g][j];
+            tf.pc[g][j] = (float)pc[g][j];
+        }
 }
 
-static int launch(mr_ctx *c, int phases, int nsteps, int only_inst, const void *aux0, const void *aux1) {
-    if (!c->bound) return c->fail(MR_ERR_STATE, "context not bound to a workspace");
+static int launch_group(mr_ctx *c, int phases, int nsteps, const int *order, int n, bool wide, const void *aux0,
+                        const void *aux1) {
     LaunchArgs a{};
     a.descs = (const InstDesc *)(c->ws + c->off_desc);
-    if (only_inst >= 0) {
-        a.order = (const int *)(c->ws + c->off_ident) + only_inst;
-        a.n = 1;
-    } else {
-        a.order = (const int *)(c->ws + c->off_order);
-        a.n = c->n();
-    }
+    a.order = order;
+    a.n = n;
+    a.wide = wide ? 1 : 0;
     a.nsteps = nsteps;
     a.phases = phases;
     a.queue = (int *)(c->ws + c->off_queue);
@@ -231,6 +240,21 @@ static int launch(mr_ctx *c, int phases, int nsteps, int only_inst, const void *
     ++c->launches;
     if (e) return c->cuda((cudaError_t)e, "kernel launch");
     return MR_OK;
+}
+
+// A launch over the instances: the queue order puts the gamma = 1 instances
+// first; each group runs in the kernel variant compiled for its stencils.
+static int launch(mr_ctx *c, int phases, int nsteps, int only_inst, const void *aux0, const void *aux1) {
+    if (!c->bound) return c->fail(MR_ERR_STATE, "context not bound to a workspace");
+    if (only_inst >= 0)
+        return launch_group(c, phases, nsteps, (const int *)(c->ws + c->off_ident) + only_inst, 1,
+                            c->hdesc[only_inst].gamma > 1, aux0, aux1);
+    const int *order = (const int *)(c->ws + c->off_order);
+    int rc = MR_OK;
+    if (c->n_narrow > 0) rc = launch_group(c, phases, nsteps, order, c->n_narrow, false, aux0, aux1);
+    if (!rc && c->n_narrow < c->n())
+        rc = launch_group(c, phases, nsteps, order + c->n_narrow, c->n() - c->n_narrow, true, aux0, aux1);
+    return rc;
 }
 
 static int read_state(mr_ctx *c, int inst, InstState *st) {
@@ -370,12 +394,15 @@ static int upload_order(mr_ctx *c) {
     std::vector<int> order(n);
     for (int i = 0; i < n; ++i) order[i] = i;
     std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
+        if ((dd[x].gamma > 1) != (dd[y].gamma > 1)) return dd[x].gamma == 1;  // kernel variant groups
         if (c->order_by_fields && dd[x].nf != dd[y].nf) return dd[x].nf > dd[y].nf;
         double cx = (double)dd[x].nf * std::ldexp(1.0, dd[x].Jmax);
         double cy = (double)dd[y].nf * std::ldexp(1.0, dd[y].Jmax);
         return cx > cy;
     });
     c->order_host = order;
+    c->n_narrow = 0;
+    for (int i = 0; i < n; ++i) c->n_narrow += dd[i].gamma == 1;
     return c->cuda(cudaMemcpyAsync(c->ws + c->off_order, c->order_host.data(), sizeof(int) * n, cudaMemcpyHostToDevice,
                                    c->stream),
                    "upload");
@@ -455,7 +482,7 @@ mr_status mr_set_initial(mr_ctx *c, const double *m, size_t count) {
 }
 
 // Host-side check that a complete-tree membership is a sibling-closed graded
-// tree (Def. Tree and Def. Graded tree with gamma = 1) before a kernel reads it.
+// tree (Def. Tree and Def. Graded tree with the instance's gamma) before a kernel reads it.
 static int check_tree(mr_ctx *c, int inst, const unsigned char *Rd) {
     const mr_instance_desc &d = c->desc[inst];
     const InstDesc &h = c->hdesc[inst];
@@ -470,7 +497,7 @@ static int check_tree(mr_ctx *c, int inst, const unsigned char *Rd) {
         for (long long k = 0; k < (1LL << l); ++k) {
             if (!at(l, k)) continue;
             if (!at(l, k ^ 1)) return c->fail(MR_ERR_ARG, "tree: cell (%d,%lld) without its sibling", l, k);
-            for (int dd = -1; dd <= 1; ++dd) {
+            for (int dd = -d.gamma; dd <= d.gamma; ++dd) {
                 long long p = (k >> 1) + dd;
                 if (d.bc == MR_BC_PERIODIC)
                     p = (p + np) % np;

@@ -280,12 +280,101 @@ __device__ __forceinline__ T predict(const T *row, long long p, int odd, int lp,
     return odd ? vp - t : vp + t;
 }
 
+// the same for a stencil of half-width gamma = 2 or 3 (coefficients c[0..gamma-1]):
+// f_p +- sum_a c_a (f_{p+a} - f_{p-a}), the sum accumulated in increasing a
+template <typename T>
+__device__ __forceinline__ T predict_g(const T *row, long long p, int odd, int lp, int bc, int gamma, const T *c) {
+    T t = c[0] * (row[wrapc(p + 1, lp, bc)] - row[wrapc(p - 1, lp, bc)]);
+#pragma unroll
+    for (int a = 2; a <= 3; ++a)
+        if (a <= gamma) t = t + c[a - 1] * (row[wrapc(p + a, lp, bc)] - row[wrapc(p - a, lp, bc)]);
+    const T vp = row[p];
+    return odd ? vp - t : vp + t;
+}
+
+// dilation by r <= 16 cells of the word x, given the words on its left (xl) and
+// right (xr) (only their r cells nearest to x are read)
+__device__ __forceinline__ uint32_t dilate_edges(uint32_t x, uint32_t xl, uint32_t xr, int r) {
+    uint32_t out = x;
+    for (int s = 1; s <= r; ++s) out |= (x << s) | (xl >> (32 - s)) | (x >> s) | (xr << (32 - s));
+    return out;
+}
+// parent bits of 6 child bits (3 parents)
+__device__ __forceinline__ uint32_t fold3(uint32_t t) {
+    t |= t >> 1;
+    return (t & 1u) | ((t >> 1) & 2u) | ((t >> 2) & 4u);
+}
+
+// First (last = false) or last finest value of one population row of the leaf
+// (l, k), by the reconstruction operator of Section 3.3 (Definition V): the
+// level-l window k - 2G .. k + 2G (tree and ghost values) is predicted level by
+// level down to Jmax around the leaf's first (last) finest cell, and wherever a
+// finer level holds a cell of the tree (the children of refined neighbours)
+// its value is used instead.  Out-of-domain cells take the value of the nearest
+// domain cell (copy boundary) or wrap (periodic), as in the prediction.
+template <typename T, int G, bool LAST>
+__device__ __noinline__ T edge_walk(const T *rowbase, int Jmin, int Jmax, int bc, const uint32_t *R, const int *woff,
+                                    const T *c, int l, long long k) {
+    constexpr int W = 4 * G + 1, C = 2 * G, E = LAST ? 1 : 0;
+    T w[W], nw[W];
+    {
+        const T *row = rowbase + cell_off(l, Jmin);
+#pragma unroll
+        for (int t = 0; t < W; ++t) w[t] = row[wrapc(k + t - C, l, bc)];
+    }
+    long long i = k;
+    for (int m = l; m < Jmax; ++m) {
+        const long long nn = 1LL << (m + 1), inext = 2 * i + E;
+        const T *row = rowbase + cell_off(m + 1, Jmin);
+        const uint32_t *Rm = R + woff[m + 1];
+        T lo = T(0), hi = T(0);  // values of the first and last cells of the level (copy boundary)
+#pragma unroll
+        for (int t = 0; t < W; ++t) {
+            // window position t is cell inext + t - C; its parent is window position pp of level m
+            const long long pos = inext + t - C;
+            const int pp = C + ((E + t - C) >> 1);
+            const bool odd = ((E + t - C) & 1) != 0;
+            long long cp = pos;
+            bool inside = true;
+            if (bc == 0)
+                cp = pos & (nn - 1);
+            else
+                inside = pos >= 0 && pos < nn;
+            T v;
+            if (inside && ((Rm[(int)(cp >> 5)] >> (cp & 31)) & 1u)) {
+                v = row[cp];
+            } else {
+                T sum = c[0] * (w[pp + 1] - w[pp - 1]);
+#pragma unroll
+                for (int a = 2; a <= G; ++a) sum = sum + c[a - 1] * (w[pp + a] - w[pp - a]);
+                v = odd ? w[pp] - sum : w[pp] + sum;
+            }
+            nw[t] = v;
+            if (pos == 0) lo = v;
+            if (pos == nn - 1) hi = v;
+        }
+        if (bc != 0) {
+#pragma unroll
+            for (int t = 0; t < W; ++t) {
+                const long long pos = inext + t - C;
+                if (pos < 0) nw[t] = lo;
+                if (pos >= nn) nw[t] = hi;
+            }
+        }
+#pragma unroll
+        for (int t = 0; t < W; ++t) w[t] = nw[t];
+        i = inext;
+    }
+    return w[C];
+}
+
 // ---------------------------------------------------------------------------
 // the instance worker; TS threads (a warp or the whole block) form the team
 
 constexpr int QMAX = 6;  // populations of the largest scheme (vectorial D1Q2^3)
 
-template <typename T, int NF, int TS>
+// WIDE: prediction stencils gamma = 2, 3 (the gamma = 1 code is a separate instantiation)
+template <typename T, int NF, int TS, bool WIDE>
 struct Worker {
     static constexpr bool WARP = TS == 32;
     static constexpr int nf = NF, q = 2 * NF;  // fields and populations of the scheme
@@ -450,6 +539,10 @@ struct Worker {
     // that bound is the detail recomputed in FP64 from the stored values, so
     // every decision equals the one the exact detail of the stored state gives.
     __device__ void details() {
+        if constexpr (WIDE) {
+            details_wide();
+            return;
+        }
         const uint32_t *lst = list(L_EVEN);
         int b = sm.seg[L_EVEN][d.Jmin + 1], e = sm.seg[L_EVEN][d.Jmax + 1];
         uint32_t *keep = mask(M_KEEP), *ref = mask(M_REF);
@@ -514,6 +607,78 @@ struct Worker {
         }
     }
 
+    // A2 with the stencil of half-width gamma = 2 or 3: the prediction sums
+    // c_a (f_{p+a} - f_{p-a}) in increasing a; the FP32 rounding band grows with
+    // the number of operations, (6 gamma + 2) u times the sum of |inputs|
+    // (3 gamma + 1 roundings, each at most u times that sum, with a factor 2 margin)
+    __device__ __noinline__ void details_wide() {
+        const uint32_t *lst = list(L_EVEN);
+        const int b = sm.seg[L_EVEN][d.Jmin + 1], e = sm.seg[L_EVEN][d.Jmax + 1], g = d.gamma;
+        const T *c = tab.pc[g];
+        uint32_t *keep = mask(M_KEEP), *ref = mask(M_REF);
+        for (int i = b + tid; i < e; i += TS) {
+            const uint32_t ent = lst[i];
+            const int l = ent >> KBITS;
+            const bool hasref = l < d.Jmax;
+            const long long k = ent & KMASK, p = k >> 1;
+            bool keepit, refit, tie = false;
+            double Dd = 0.0;
+            float Df = 0.0f, B = 0.0f;
+            for (int h = 0; h < q; ++h) {
+                const T *rc = row(h, l - 1);
+                T sum = T(0);
+                float mag = 0.0f;
+                for (int a = 1; a <= g; ++a) {
+                    const T vr = rc[wrapc(p + a, l - 1, d.bc)], vl = rc[wrapc(p - a, l - 1, d.bc)];
+                    sum = a == 1 ? c[0] * (vr - vl) : sum + c[a - 1] * (vr - vl);
+                    if constexpr (sizeof(T) == 4) mag = mag + fabsf(vr) + fabsf(vl);
+                }
+                const T vk = row(h, l)[k], vp = rc[p];
+                if constexpr (sizeof(T) == 8) {
+                    Dd = fmax(Dd, fabs(vk - (vp + sum)));
+                } else {
+                    Df = fmaxf(Df, fabsf(vk - (vp + sum)));
+                    B = fmaxf(B, fabsf(vk) + fabsf(vp) + mag);
+                }
+            }
+            if constexpr (sizeof(T) == 8) {
+                const double el = sm.eps_l[l], bl = sm.big_l[l];
+                keepit = Dd >= el;
+                refit = hasref && Dd >= bl;
+                tie = fabs(Dd - el) <= 1e-12 * el || (hasref && fabs(Dd - bl) <= 1e-12 * bl);
+            } else {
+                B *= (float)(6 * g + 2) * 0x1p-24f;
+                const float el = sm.eps_f[l], bl = sm.big_f[l];
+                const bool amb = fabsf(Df - el) <= B + el * 0x1p-22f || (hasref && fabsf(Df - bl) <= B + bl * 0x1p-22f);
+                if (amb) {
+                    for (int h = 0; h < q; ++h) {
+                        const T *rc = row(h, l - 1);
+                        double sum = 0.0;
+                        for (int a = 1; a <= g; ++a)
+                            sum = a == 1 ? (double)c[0] * ((double)rc[wrapc(p + 1, l - 1, d.bc)] - (double)rc[wrapc(p - 1, l - 1, d.bc)])
+                                         : sum + (double)c[a - 1] * ((double)rc[wrapc(p + a, l - 1, d.bc)] -
+                                                                     (double)rc[wrapc(p - a, l - 1, d.bc)]);
+                        Dd = fmax(Dd, fabs((double)row(h, l)[k] - ((double)rc[p] + sum)));
+                    }
+                    const double e64 = sm.eps_l[l], b64 = sm.big_l[l];
+                    keepit = Dd >= e64;
+                    refit = hasref && Dd >= b64;
+                    tie = fabs(Dd - e64) <= 1e-12 * e64 || (hasref && fabs(Dd - b64) <= 1e-12 * b64);
+                } else {
+                    keepit = Df >= el;
+                    refit = hasref && Df >= bl;
+                }
+            }
+            if (tie) atomicAdd(&sm.near_ties, 1);
+            if (keepit) {
+                const int w = (int)(k >> 5);
+                const uint32_t bits = 3u << (k & 31);
+                atomicOr(&keep[sm.woff[l] + w], bits);
+                if (refit) atomicOr(&ref[sm.woff[l] + w], bits);
+            }
+        }
+    }
+
     // ---- A3: R(H(T)) per word ------------------------------------------------
     __device__ void enlarge(uint32_t *Rn) {
         const uint32_t *keep = mask(M_KEEP), *ref = mask(M_REF);
@@ -545,17 +710,28 @@ struct Worker {
     // grade = false only re-derives the marks of a tree known to be graded.
     __device__ void grade_and_mark(uint32_t *Rn, const uint32_t *Ro, bool grade) {
         uint32_t *LF = mask(M_LEAF), *PR = mask(M_PRED), *GH = mask(M_GH);
+        const int g = d.gamma;
         const int lbig = d.Jmin > 6 ? d.Jmin : 6;
         for (int l = d.Jmax; l >= lbig; --l) {
             const int Wl = 1 << (l - 5);
             const uint32_t *rl = Rn + sm.woff[l];
             if (grade && l > d.Jmin + 1) {
                 uint32_t *rp = Rn + sm.woff[l - 1];
-                for (int wp = tid; wp < (Wl >> 1); wp += TS) {
-                    uint32_t x = fold2(rl[2 * wp], rl[2 * wp + 1]);
-                    bool eL = (word_bc(rl, 2 * wp - 1, Wl, d.bc) >> 30) != 0u;  // children of parent 32 wp - 1
-                    bool eR = (word_bc(rl, 2 * wp + 2, Wl, d.bc) & 3u) != 0u;   // children of parent 32 wp + 32
-                    rp[wp] |= pairexpand(dilate1_edges(x, eL, eR));
+                if constexpr (!WIDE) {
+                    for (int wp = tid; wp < (Wl >> 1); wp += TS) {
+                        uint32_t x = fold2(rl[2 * wp], rl[2 * wp + 1]);
+                        bool eL = (word_bc(rl, 2 * wp - 1, Wl, d.bc) >> 30) != 0u;  // children of parent 32 wp - 1
+                        bool eR = (word_bc(rl, 2 * wp + 2, Wl, d.bc) & 3u) != 0u;   // children of parent 32 wp + 32
+                        rp[wp] |= pairexpand(dilate1_edges(x, eL, eR));
+                    }
+                } else {
+                    for (int wp = tid; wp < (Wl >> 1); wp += TS) {
+                        const uint32_t x = fold2(rl[2 * wp], rl[2 * wp + 1]);
+                        // parents 29..31 of the word on the left, 0..2 of the word on the right
+                        const uint32_t xl = fold3(word_bc(rl, 2 * wp - 1, Wl, d.bc) >> 26) << 29;
+                        const uint32_t xr = fold3(word_bc(rl, 2 * wp + 2, Wl, d.bc) & 63u);
+                        rp[wp] |= pairexpand(dilate_edges(x, xl, xr, g));
+                    }
                 }
             }
             const uint32_t *rol = Ro + sm.woff[l];
@@ -566,6 +742,27 @@ struct Worker {
                     lfl[wi] = r;
                     prl[wi] = r & ~rol[wi];
                     ghl[wi] = 0u;
+                }
+            } else if constexpr (WIDE) {
+                const int Wc = Wl << 1;
+                const uint32_t *rc = Rn + sm.woff[l + 1], *pc = PR + sm.woff[l + 1], *gc = GH + sm.woff[l + 1];
+                for (int wi = tid; wi < Wl; wi += TS) {
+                    const uint32_t r = rl[wi], ro = rol[wi];
+                    const uint32_t lf = r & ~fold2(rc[2 * wi], rc[2 * wi + 1]);
+                    // leaf bits of the 16 cells of each neighbouring word next to this one
+                    const uint32_t cL = word_bc(rc, 2 * wi - 1, Wc, d.bc), cR = word_bc(rc, 2 * wi + 2, Wc, d.bc);
+                    const uint32_t lfL = word_bc(rl, wi - 1, Wl, d.bc) & ~(compact_even(cL | (cL >> 1)) << 16);
+                    const uint32_t lfR = word_bc(rl, wi + 1, Wl, d.bc) & ~compact_even(cR | (cR >> 1));
+                    const uint32_t gw = dilate_edges(lf, lfL, lfR, 2 * g);  // reconstruction windows
+                    const uint32_t pd = dilate_edges(fold2(pc[2 * wi], pc[2 * wi + 1]),
+                                                     fold3(word_bc(pc, 2 * wi - 1, Wc, d.bc) >> 26) << 29,
+                                                     fold3(word_bc(pc, 2 * wi + 2, Wc, d.bc) & 63u), g);
+                    const uint32_t gd = dilate_edges(fold2(gc[2 * wi], gc[2 * wi + 1]),
+                                                     fold3(word_bc(gc, 2 * wi - 1, Wc, d.bc) >> 26) << 29,
+                                                     fold3(word_bc(gc, 2 * wi + 2, Wc, d.bc) & 63u), g);
+                    lfl[wi] = lf;
+                    prl[wi] = (lf | pd) & ~ro;
+                    ghl[wi] = (gw | gd) & ~r;
                 }
             } else {
                 const int Wc = Wl << 1;
@@ -603,10 +800,13 @@ struct Worker {
         const uint32_t vb = n == 32 ? 0xFFFFFFFFu : ((1u << n) - 1u);
         uint32_t out = x;
         for (int s = 1; s <= r; ++s) {
-            if (d.bc == 0)
-                out |= ((x << s) | (x >> (n - s)) | (x >> s) | (x << (n - s))) & vb;
-            else
+            if (d.bc == 0) {
+                // rotations within the level (a wide stencil's reach may exceed n)
+                const int sm_ = WIDE ? s % n : s;
+                if (sm_) out |= ((x << sm_) | (x >> (n - sm_)) | (x >> sm_) | (x << (n - sm_))) & vb;
+            } else {
                 out |= ((x << s) & vb) | (x >> s);
+            }
         }
         return out;
     }
@@ -618,6 +818,7 @@ struct Worker {
     // one level of at most 32 cells (a single word): grading of level l-1 and
     // marks of level l, as in the word-wise sweep above
     __device__ void small_level(uint32_t *Rn, const uint32_t *Ro, int l, bool grade) {
+        const int gam = WIDE ? d.gamma : 1;
         uint32_t *LF = mask(M_LEAF), *PR = mask(M_PRED), *GH = mask(M_GH);
         const int n = 1 << l, o = sm.woff[l];
         const uint32_t vb = n == 32 ? 0xFFFFFFFFu : ((1u << n) - 1u);
@@ -625,15 +826,15 @@ struct Worker {
         if (grade && l > d.Jmin + 1) {
             const int np = n >> 1;
             const uint32_t vbp = (1u << np) - 1u;
-            Rn[sm.woff[l - 1]] |= pairexpand(dil_small(fold2(r, 0u), np, 1)) & vbp;
+            Rn[sm.woff[l - 1]] |= pairexpand(dil_small(fold2(r, 0u), np, gam)) & vbp;
         }
         const uint32_t ro = Ro[o];
         uint32_t lf = r, pr, gh = 0u;
         if (l < d.Jmax) {
             const int oc = sm.woff[l + 1];
             lf = r & ~fold_small(Rn + oc, l);
-            pr = (lf | dil_small(fold_small(PR + oc, l), n, 1)) & ~ro;
-            gh = (dil_small(lf, n, 2) | dil_small(fold_small(GH + oc, l), n, 1)) & ~r;
+            pr = (lf | dil_small(fold_small(PR + oc, l), n, gam)) & ~ro;
+            gh = (dil_small(lf, n, 2 * gam) | dil_small(fold_small(GH + oc, l), n, gam)) & ~r;
         } else {
             pr = lf & ~ro;
         }
@@ -722,9 +923,16 @@ struct Worker {
         for (int i = b + tid; i < e; i += TS) {
             long long k = lst[i] & KMASK;
             T v[QMAX];
+            if constexpr (!WIDE) {
 #pragma unroll
-            for (int h = 0; h < QMAX; ++h)
-                if (h < q) v[h] = predict<T>(row(h, l - 1), k >> 1, (int)(k & 1), l - 1, d.bc);
+                for (int h = 0; h < QMAX; ++h)
+                    if (h < q) v[h] = predict<T>(row(h, l - 1), k >> 1, (int)(k & 1), l - 1, d.bc);
+            } else {
+#pragma unroll
+                for (int h = 0; h < QMAX; ++h)
+                    if (h < q)
+                        v[h] = predict_g<T>(row(h, l - 1), k >> 1, (int)(k & 1), l - 1, d.bc, d.gamma, tab.pc[d.gamma]);
+            }
 #pragma unroll
             for (int h = 0; h < QMAX; ++h)
                 if (h < q) row(h, l)[k] = v[h];
@@ -785,6 +993,10 @@ struct Worker {
 
     // S4: first / last finest-cell values of every leaf -> Phi
     __device__ void reconstruct_edges() {
+        if constexpr (WIDE) {
+            reconstruct_wide();
+            return;
+        }
         const uint32_t *R = mask(sm.cur);
         const uint32_t *leaves = list(L_LEAF);
         for (int i = tid; i < sm.nleaf; i += TS) {
@@ -841,6 +1053,48 @@ struct Worker {
                             rlast = dot4(cf[3], vm1, cf[2], v0, cf[1], vp1, cf[0], r[wrapc(k + 2, l, d.bc)]);
                         }
                     }
+                }
+                T *ph = Phi + (long long)h * (d.N + 1);
+                if (plus) {
+                    long long ix = (k + 1) << dj;
+                    if (d.bc == 0) ix &= d.N - 1;
+                    ph[ix] = rlast;
+                    if (at_left) ph[0] = rfirst;
+                } else {
+                    ph[k << dj] = rfirst;
+                    if (at_right) ph[d.N] = rlast;
+                }
+            }
+        }
+    }
+
+    // S4 with the stencil of half-width gamma = 2 or 3: the first / last finest
+    // values by the level-by-level reconstruction (edge_walk) instead of tables
+    __device__ __noinline__ void reconstruct_wide() {
+        const uint32_t *R = mask(sm.cur);
+        const uint32_t *leaves = list(L_LEAF);
+        const int g = d.gamma;
+        const T *c = tab.pc[g];
+        for (int i = tid; i < sm.nleaf; i += TS) {
+            const uint32_t ent = leaves[i];
+            const int l = ent >> KBITS;
+            const long long k = ent & KMASK;
+            const int dj = d.Jmax - l;
+            const bool at_left = d.bc == 1 && k == 0, at_right = d.bc == 1 && k == (1LL << l) - 1;
+            for (int h = 0; h < q; ++h) {
+                const T *rb = V + (long long)h * d.S;
+                const bool plus = (h & 1) == 0;  // velocity +lambda
+                const bool need_first = !plus || at_left, need_last = plus || at_right;
+                T rfirst = T(0), rlast = T(0);
+                if (dj == 0) {
+                    rfirst = rlast = row(h, l)[k];
+                } else {
+                    if (need_first)
+                        rfirst = g == 2 ? edge_walk<T, 2, false>(rb, d.Jmin, d.Jmax, d.bc, R, sm.woff, c, l, k)
+                                        : edge_walk<T, 3, false>(rb, d.Jmin, d.Jmax, d.bc, R, sm.woff, c, l, k);
+                    if (need_last)
+                        rlast = g == 2 ? edge_walk<T, 2, true>(rb, d.Jmin, d.Jmax, d.bc, R, sm.woff, c, l, k)
+                                       : edge_walk<T, 3, true>(rb, d.Jmin, d.Jmax, d.bc, R, sm.woff, c, l, k);
                 }
                 T *ph = Phi + (long long)h * (d.N + 1);
                 if (plus) {
@@ -1022,7 +1276,9 @@ struct Worker {
             const uint32_t *rl = R + sm.woff[l];
             for (long long k = tid; k < n; k += TS)
                 if (!((rl[k >> 5] >> (k & 31)) & 1u))
-                    for (int h = 0; h < q; ++h) row(h, l)[k] = predict<T>(row(h, l - 1), k >> 1, (int)(k & 1), l - 1, d.bc);
+                    for (int h = 0; h < q; ++h)
+                        row(h, l)[k] = predict_g<T>(row(h, l - 1), k >> 1, (int)(k & 1), l - 1, d.bc, d.gamma,
+                                                    tab.pc[d.gamma]);
             sync();
         }
         for (long long k = tid; k < d.N; k += TS)
@@ -1101,10 +1357,11 @@ __device__ void store_instance(TeamSmem<T> &sm, int tid) {
         __syncthreads();
 }
 
-template <typename T, int NF, int TS>
-__device__ void run_instance(TeamSmem<T> &sm, const Tables<T> &tab, BlockScratch &bx, const LaunchArgs &a, int tid,
+// one instance for the launch's steps
+template <typename T, int NF, int TS, bool WIDE>
+__device__ __forceinline__ void run_instance(TeamSmem<T> &sm, const Tables<T> &tab, BlockScratch &bx, const LaunchArgs &a, int tid,
                              uint32_t *masks) {
-    Worker<T, NF, TS> w(sm, tab, bx, tid, masks);
+    Worker<T, NF, TS, WIDE> w(sm, tab, bx, tid, masks);
     if (a.phases & PH_INIT_FULL) w.init_full((const double *)a.aux0 + sm.d.m_off);
     if (a.phases & PH_INIT_STATE) w.init_state((const unsigned char *)a.aux0, (const double *)a.aux1);
     for (int n = 0; n < a.nsteps; ++n) {
@@ -1117,7 +1374,7 @@ __device__ void run_instance(TeamSmem<T> &sm, const Tables<T> &tab, BlockScratch
 // Bitmasks live in shared memory (smask, room for `cap` words per mask) when the
 // instance fits: the current tree is copied in at the start and back at the
 // end, KEEP / REF start cleared, the other masks are rebuilt by every step.
-template <typename T, int TS>
+template <typename T, int TS, bool WIDE>
 __device__ void run_team(TeamSmem<T> &sm, const Tables<T> &tab, BlockScratch &bx, const LaunchArgs &a,
                          const InstDesc &dg, int tid, uint32_t *smask, int cap) {
     load_instance<T, TS>(sm, dg, tid);
@@ -1135,9 +1392,9 @@ __device__ void run_team(TeamSmem<T> &sm, const Tables<T> &tab, BlockScratch &bx
         __syncthreads();
     }
     switch (sm.d.nf) {
-    case 1: run_instance<T, 1, TS>(sm, tab, bx, a, tid, masks); break;
-    case 2: run_instance<T, 2, TS>(sm, tab, bx, a, tid, masks); break;
-    default: run_instance<T, 3, TS>(sm, tab, bx, a, tid, masks); break;
+    case 1: run_instance<T, 1, TS, WIDE>(sm, tab, bx, a, tid, masks); break;
+    case 2: run_instance<T, 2, TS, WIDE>(sm, tab, bx, a, tid, masks); break;
+    default: run_instance<T, 3, TS, WIDE>(sm, tab, bx, a, tid, masks); break;
     }
     if (local) {
         uint32_t *gr = sm.d.masks + (long long)sm.cur * W;
@@ -1148,8 +1405,10 @@ __device__ void run_team(TeamSmem<T> &sm, const Tables<T> &tab, BlockScratch &bx
 }
 
 // Persistent kernel: each block takes instances from the queue (largest first)
-// and advances one at a time with all its threads.
-template <typename T, int NT, int MINB>
+// and advances one at a time with all its threads.  WIDE: the instances of the
+// launch use prediction stencils gamma = 2 or 3 (a separate kernel, so the
+// gamma = 1 code is compiled on its own).
+template <typename T, int NT, int MINB, bool WIDE>
 __global__ void __launch_bounds__(NT, MINB) mr_persistent(LaunchArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     BlockSmem<T, NT> &bs = *reinterpret_cast<BlockSmem<T, NT> *>(smem_raw);
@@ -1167,7 +1426,8 @@ __global__ void __launch_bounds__(NT, MINB) mr_persistent(LaunchArgs a) {
         const int idx = bs.idx;
         __syncthreads();
         if (idx >= a.n) return;
-        run_team<T, NT>(bs.team, bs.tab, bs.scratch, a, a.descs[a.order[idx]], threadIdx.x, smask, a.smem_mask_words);
+        run_team<T, NT, WIDE>(bs.team, bs.tab, bs.scratch, a, a.descs[a.order[idx]], threadIdx.x, smask,
+                              a.smem_mask_words);
     }
 }
 
@@ -1181,7 +1441,10 @@ __global__ void __launch_bounds__(NT, MINB) mr_persistent(LaunchArgs a) {
         return base + (size_t)mask_words * mrg::NMASK * sizeof(uint32_t);                          \
     }                                                                                             \
     static int mrg_attr_##TAG() {                                                                 \
-        static int rc = (int)cudaFuncSetAttribute(mrg::mr_persistent<T, NT, MINB>,                \
+        static int rc = (int)cudaFuncSetAttribute(mrg::mr_persistent<T, NT, MINB, false>,         \
+                                                  cudaFuncAttributeMaxDynamicSharedMemorySize,     \
+                                                  227 * 1024) |                                    \
+                        (int)cudaFuncSetAttribute(mrg::mr_persistent<T, NT, MINB, true>,          \
                                                   cudaFuncAttributeMaxDynamicSharedMemorySize,     \
                                                   227 * 1024);                                     \
         return rc;                                                                                \
@@ -1189,13 +1452,16 @@ __global__ void __launch_bounds__(NT, MINB) mr_persistent(LaunchArgs a) {
     int mrg_launch_##TAG(int grid, const mrg::LaunchArgs &a, cudaStream_t s) {                     \
         int rc = mrg_attr_##TAG();                                                                \
         if (rc) return rc;                                                                        \
-        mrg::mr_persistent<T, NT, MINB><<<grid, NT, mrg_dyn_##TAG(a.smem_mask_words), s>>>(a);      \
+        if (a.wide)                                                                               \
+            mrg::mr_persistent<T, NT, MINB, true><<<grid, NT, mrg_dyn_##TAG(a.smem_mask_words), s>>>(a); \
+        else                                                                                      \
+            mrg::mr_persistent<T, NT, MINB, false><<<grid, NT, mrg_dyn_##TAG(a.smem_mask_words), s>>>(a); \
         return (int)cudaGetLastError();                                                           \
     }                                                                                             \
     int mrg_occ_##TAG(int mask_words, int *nb) {                                                  \
         int rc = mrg_attr_##TAG();                                                                \
         if (rc) return rc;                                                                        \
-        return (int)cudaOccupancyMaxActiveBlocksPerMultiprocessor(nb, mrg::mr_persistent<T, NT, MINB>, \
+        return (int)cudaOccupancyMaxActiveBlocksPerMultiprocessor(nb, mrg::mr_persistent<T, NT, MINB, false>, \
                                                                    NT, mrg_dyn_##TAG(mask_words)); \
     }                                                                                             \
     size_t mrg_smem_##TAG(int mask_words) { return mrg_dyn_##TAG(mask_words); }

@@ -51,7 +51,7 @@ extern "C" mr_status mr_run_static(const mr_instance_desc *desc, int precision, 
         return fail(MR_ERR_ARG, "mr_run_static: need a descriptor, input and output pointers, nsteps >= 0");
     const mr_instance_desc &d = *desc;
     const int nf = nfields(d.eq);
-    if (d.Jmin < 2 || d.Jmax < d.Jmin || d.Jmax > MAXLEV || d.gamma != 1 || nf == 0 || d.mu_bar < 0 ||
+    if (d.Jmin < 2 || d.Jmax < d.Jmin || d.Jmax > MAXLEV || d.gamma < 1 || d.gamma > 3 || nf == 0 || d.mu_bar < 0 ||
         (d.bc != MR_BC_PERIODIC && d.bc != MR_BC_COPY) || !(d.eps >= 0.0) || !(d.b > d.a) || !(d.lambda > 0.0))
         return fail(MR_ERR_ARG, "mr_run_static: invalid instance description");
     for (int j = 0; j < nf; ++j)
@@ -112,6 +112,7 @@ extern "C" mr_status mr_run_static(const mr_instance_desc *desc, int precision, 
     h.eq = d.eq;
     h.nf = nf;
     h.mu_bar = d.mu_bar;
+    h.gamma = d.gamma;
     h.Wtot = W;
     h.eps = d.eps;
     h.a = d.a;
@@ -159,6 +160,7 @@ extern "C" mr_status mr_run_static(const mr_instance_desc *desc, int precision, 
     a.queue = (int *)(base + oQueue);
     a.tables = base + oTab + (fp32 ? sizeof(Tables<double>) : 0);
     a.smem_mask_words = W <= fit ? W : 0;
+    a.wide = d.gamma > 1 ? 1 : 0;
     const int phases[3] = {PH_INIT_FULL, PH_ADAPT | PH_STEP, PH_FINEST};
     const int steps[3] = {0, nsteps, 0};
     for (int i = 0; i < 3; ++i) {

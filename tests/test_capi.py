@@ -34,7 +34,7 @@ def test_argument_validation():
     h = ctypes.c_void_p()
     assert L.mr_mesh_init(ctypes.byref(h), 1, 8, 1, 1e-4, -1.0, 1.0, 0, 0, 0) == capi.MR_ERR_ARG
     assert L.mr_mesh_init(ctypes.byref(h), 2, 30, 1, 1e-4, -1.0, 1.0, 0, 0, 0) == capi.MR_ERR_ARG
-    assert L.mr_mesh_init(ctypes.byref(h), 2, 8, 2, 1e-4, -1.0, 1.0, 0, 0, 0) == capi.MR_ERR_ARG
+    assert L.mr_mesh_init(ctypes.byref(h), 2, 8, 4, 1e-4, -1.0, 1.0, 0, 0, 0) == capi.MR_ERR_ARG
     assert L.mr_mesh_init(ctypes.byref(h), 2, 8, 1, -1.0, -1.0, 1.0, 0, 0, 0) == capi.MR_ERR_ARG
     assert L.mr_mesh_init(ctypes.byref(h), 2, 8, 1, 1e-4, 1.0, -1.0, 0, 0, 0) == capi.MR_ERR_ARG
     buf = ctypes.create_string_buffer(256)
@@ -74,6 +74,14 @@ def test_batch_creation_checks_every_descriptor():
     h = ctypes.c_void_p()
     assert L.mr_batch_create(ctypes.byref(h), descs, 3, capi.MR_FP32_MIXED) == capi.MR_OK
     L.mr_destroy(h)
+    # prediction stencils gamma = 1, 2, 3 are built; 0 and 4 are refused
+    descs[1].gamma, descs[2].gamma = 2, 3
+    assert L.mr_batch_create(ctypes.byref(h), descs, 3, capi.MR_FP64) == capi.MR_OK
+    L.mr_destroy(h)
+    for bad in (0, 4):
+        descs[1].gamma = bad
+        assert L.mr_batch_create(ctypes.byref(h), descs, 3, capi.MR_FP64) == capi.MR_ERR_ARG
+    descs[1].gamma = 2
     descs[2].s[0] = 2.5
     assert L.mr_batch_create(ctypes.byref(h), descs, 3, capi.MR_FP64) == capi.MR_ERR_ARG
     buf = ctypes.create_string_buffer(256)

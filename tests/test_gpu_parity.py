@@ -353,3 +353,90 @@ def test_scalar_tests_full_run_errors(test):
             assert_same_leaves(lvs, o, tol=1e-11)
             assert abs(d - d_oracle) <= 1e-10
         assert E / d > 5.0, (test, prec, E, d)
+
+
+GAMMA_CASES = [
+    ("g2-euler-periodic", lambda: W.random_smooth(10, W.EQ_EULER, seed=70, eps=3e-4).with_(gamma=2)),
+    ("g2-burgers-copy", lambda: W.random_smooth(11, W.EQ_BURGERS, seed=71, eps=1e-4, bc=W.BC_COPY).with_(gamma=2)),
+    ("g3-sw-copy", lambda: W.random_smooth(10, W.EQ_SW, seed=72, eps=1e-4, bc=W.BC_COPY).with_(gamma=3)),
+    ("g3-adv-periodic", lambda: W.random_smooth(10, W.EQ_ADVECTION, seed=73, eps=1e-4).with_(gamma=3)),
+    ("g3-euler-jmin4", lambda: W.random_smooth(9, W.EQ_EULER, seed=74, eps=1e-4, Jmin=4, bc=W.BC_COPY).with_(gamma=3)),
+    ("g2-testIV", lambda: W.scalar_test("IV").with_(gamma=2)),
+]
+
+
+@pytest.mark.parametrize("name,make", GAMMA_CASES, ids=[c[0] for c in GAMMA_CASES])
+def test_wide_stencil_lockstep_parity(name, make):
+    """Prediction stencils gamma = 2, 3 (Section 3.1): meshes bit for bit and
+    populations within 1e-12 of the oracle, step by step from identical states."""
+    inst = make()
+    s = _solver(inst)
+    o = O.Oracle(params_of(inst))
+    for n in range(8):
+        R, vals, _ = gpu_state(s)
+        o.set_state(R, vals)
+        o.step()
+        s.advance(1)
+        R2, _, lvs = gpu_state(s)
+        assert np.array_equal(R2, o.get_state()[0]), f"step {n}: mesh differs"
+        assert_same_leaves(lvs, o)
+
+
+@pytest.mark.parametrize("name,make", GAMMA_CASES, ids=[c[0] for c in GAMMA_CASES])
+def test_wide_stencil_free_running_parity(name, make):
+    inst = make()
+    s = _solver(inst)
+    o = oracle_of(inst)
+    for n in range(30):
+        o.step()
+        s.advance(1)
+    R, _, lvs = gpu_state(s)
+    assert np.array_equal(R, o.get_state()[0])
+    assert_same_leaves(lvs, o, tol=1e-11)
+    assert np.max(np.abs(s.finest() - o.finest_moments())) < 1e-11
+    m, res = s.audit()
+    assert np.allclose(m, o.mass(), rtol=1e-12, atol=1e-13)
+
+
+@pytest.mark.parametrize("gamma,bc", [(2, W.BC_PERIODIC), (3, W.BC_COPY), (3, W.BC_PERIODIC)])
+def test_wide_stencil_arbitrary_graded_trees(gamma, bc):
+    """Random gamma-graded trees with many level jumps: the reconstruction walk,
+    the ghost marks and the transfer against the oracle's Definition V."""
+    rng = np.random.default_rng(80 + gamma + 3 * bc)
+    inst = W.random_smooth(10, W.EQ_EULER, seed=81, bc=bc, eps=1e-4).with_(gamma=gamma)
+    s = _solver(inst)
+    o = O.Oracle(params_of(inst))
+    R = random_graded_tree(inst.Jmin, inst.Jmax, rng, density=0.3, bc=bc, gamma=gamma)
+    base = O.equilibrium(params_of(inst), np.array([[1.0], [0.1], [2.0]]))[:, :1]
+    vals = base + 0.02 * rng.normal(size=(inst.q, o.S))
+    s.set_state(0, R, vals)
+    o.set_state(R, vals)
+    o.lbm_step()
+    s.lbm_step()
+    _, _, lvs = gpu_state(s)
+    assert_same_leaves(lvs, o)
+    for n in range(4):
+        R, vals, _ = gpu_state(s)
+        o.set_state(R, vals)
+        o.step()
+        s.advance(1)
+        R2, _, lvs = gpu_state(s)
+        assert np.array_equal(R2, o.get_state()[0])
+        assert_same_leaves(lvs, o)
+
+
+def test_wide_stencil_fp32_and_batch():
+    insts = [i.with_(gamma=1 + (j % 3)) for j, i in enumerate(W.batch(n=18, seed=90, Jmax_range=(6, 10)))]
+    for j, i in enumerate(W.batch(n=18, seed=90, Jmax_range=(6, 10))):
+        insts[j].m0 = i.m0
+    s64, s32 = _solver(insts), _solver(insts, precision=MR_FP32_MIXED)
+    s64.advance(10)
+    s32.advance(10)
+    for i in range(len(insts)):
+        o = oracle_of(insts[i])
+        o.step(10)
+        R, _, lvs = gpu_state(s64, i)
+        assert np.array_equal(R, o.get_state()[0]), i
+        assert_same_leaves(lvs, o, tol=1e-11)
+        err = insts[i].dx * np.abs(s32.finest(i) - o.finest_moments()).sum(axis=1)
+        assert np.all(err < 1e-4), (i, err)
