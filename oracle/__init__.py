@@ -27,7 +27,9 @@ _LIB = os.path.join(_HERE, "liborc.so")
 
 BC_PERIODIC, BC_COPY = 0, 1
 EQ_ADVECTION, EQ_BURGERS, EQ_SW, EQ_EULER = 0, 1, 2, 3
-NFIELDS = {EQ_ADVECTION: 1, EQ_BURGERS: 1, EQ_SW: 2, EQ_EULER: 3}
+EQ_SW_D1Q3, EQ_SW_D1Q5 = 4, 5  # shallow water, one velocity set for h and hu (Section 5.2)
+NFIELDS = {EQ_ADVECTION: 1, EQ_BURGERS: 1, EQ_SW: 2, EQ_EULER: 3, EQ_SW_D1Q3: 2, EQ_SW_D1Q5: 2}
+NPOP = {EQ_ADVECTION: 2, EQ_BURGERS: 2, EQ_SW: 4, EQ_EULER: 6, EQ_SW_D1Q3: 3, EQ_SW_D1Q5: 5}
 
 
 def build(force: bool = False) -> str:
@@ -65,6 +67,7 @@ def lib():
         sp = P(_Params)
         sig = {
             "orc_nfields": (ctypes.c_int, [ctypes.c_int]),
+            "orc_npop": (ctypes.c_int, [ctypes.c_int]),
             "orc_create": (ctypes.c_void_p, [sp]),
             "orc_free": (None, [ctypes.c_void_p]),
             "orc_total_cells": (ctypes.c_long, [ctypes.c_void_p]),
@@ -138,7 +141,7 @@ class Params:
 
     @property
     def q(self) -> int:
-        return 2 * self.nf
+        return NPOP[self.eq]
 
 
 def level_offsets(Jmin: int, Jmax: int) -> list[int]:

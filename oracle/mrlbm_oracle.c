@@ -30,7 +30,11 @@
  *     R(T(Lambda^n)), rule (b) on every kept pair; thresholds compare with >=;
  *   - the vectorial D1Q2^n schemes number the moments of field i as
  *     (m^{2i} conserved, m^{2i+1} relaxed) and the populations as
- *     (f^{2i}: velocity +lambda, f^{2i+1}: velocity -lambda).
+ *     (f^{2i}: velocity +lambda, f^{2i+1}: velocity -lambda);
+ *   - the D1Q3 / D1Q5 shallow water schemes (Section 5.2) number the
+ *     populations as the paper's velocities (0, lambda, -lambda, 2 lambda,
+ *     -2 lambda) and use its parameters alpha = beta = 1; the enlargement width
+ *     sigma is the largest |v^h| / lambda of the scheme (2 for D1Q5).
  */
 #include "mrlbm_oracle.h"
 
@@ -60,9 +64,34 @@ int orc_nfields(int eq) {
     case ORC_EQ_BURGERS: return 1;
     case ORC_EQ_SW: return 2;
     case ORC_EQ_EULER: return 3;
+    case ORC_EQ_SW_D1Q3:
+    case ORC_EQ_SW_D1Q5: return 2;
     default: return 0;
     }
 }
+
+int orc_npop(int eq) {
+    switch (eq) {
+    case ORC_EQ_SW_D1Q3: return 3;
+    case ORC_EQ_SW_D1Q5: return 5;
+    default: return 2 * orc_nfields(eq);
+    }
+}
+
+/* normalised velocities w^h = v^h / lambda of the scheme; returns q */
+static int velocities(int eq, int *w) {
+    if (eq == ORC_EQ_SW_D1Q3 || eq == ORC_EQ_SW_D1Q5) {
+        const int v[5] = {0, 1, -1, 2, -2};
+        int q = orc_npop(eq);
+        for (int h = 0; h < q; ++h) w[h] = v[h];
+        return q;
+    }
+    int q = orc_npop(eq);
+    for (int h = 0; h < q; ++h) w[h] = (h & 1) ? -1 : 1;
+    return q;
+}
+
+static int is_dq(int eq) { return eq == ORC_EQ_SW_D1Q3 || eq == ORC_EQ_SW_D1Q5; }
 
 static long ncells(int l) { return 1L << l; }
 
@@ -226,10 +255,80 @@ static void equilibria(const orc_params *p, const double *mc, double *meq) {
     }
 }
 
+/* D1Q3 / D1Q5 (Section 5.2): moment matrix M[i][h] = (v^h)^i, i = 0 .. q-1,
+ * and its inverse by Gauss-Jordan elimination with partial pivoting. */
+static void dq_matrices(const orc_params *p, int q, double M[5][5], double Mi[5][5]) {
+    int w[ORC_MAXQ];
+    velocities(p->eq, w);
+    double A[5][10];
+    for (int i = 0; i < q; ++i)
+        for (int h = 0; h < q; ++h) {
+            double v = w[h] * p->lambda, x = 1.0;
+            for (int e = 0; e < i; ++e) x = x * v;
+            M[i][h] = x;
+            A[i][h] = x;
+            A[i][q + h] = i == h ? 1.0 : 0.0;
+        }
+    for (int c = 0; c < q; ++c) {
+        int piv = c;
+        for (int r = c + 1; r < q; ++r)
+            if (fabs(A[r][c]) > fabs(A[piv][c])) piv = r;
+        for (int j = 0; j < 2 * q; ++j) {
+            double t = A[c][j];
+            A[c][j] = A[piv][j];
+            A[piv][j] = t;
+        }
+        double d = A[c][c];
+        for (int j = 0; j < 2 * q; ++j) A[c][j] = A[c][j] / d;
+        for (int r = 0; r < q; ++r)
+            if (r != c) {
+                double fct = A[r][c];
+                for (int j = 0; j < 2 * q; ++j) A[r][j] = A[r][j] - fct * A[c][j];
+            }
+    }
+    for (int i = 0; i < q; ++i)
+        for (int j = 0; j < q; ++j) Mi[i][j] = A[i][q + j];
+}
+
+/* equilibria of the relaxed moments m^2 (, m^3, m^4): h u^2 + g h^2 / 2 with
+ * h = m^0, h u = m^1 (, alpha lambda^2 m^1, beta lambda^2 m^{2,eq}) */
+static void dq_equilibria(const orc_params *p, int q, const double *m, double *meq) {
+    meq[2] = (m[1] * m[1]) / m[0] + (0.5 * p->eqp) * (m[0] * m[0]);
+    if (q == 5) {
+        double l2 = p->lambda * p->lambda;
+        meq[3] = 1.0 * l2 * m[1];
+        meq[4] = 1.0 * l2 * meq[2];
+    }
+}
+
+/* collision of one cell: m = M f, m^i* = (1 - s^i) m^i + s^i m^{i,eq} for
+ * i >= 2, f* = M^{-1} m* */
+static void dq_collide(const orc_params *p, double *f, long stride) {
+    int q = orc_npop(p->eq);
+    double M[5][5], Mi[5][5], m[5], meq[5];
+    dq_matrices(p, q, M, Mi);
+    for (int i = 0; i < q; ++i) {
+        double acc = 0.0;
+        for (int h = 0; h < q; ++h) acc = acc + M[i][h] * f[h * stride];
+        m[i] = acc;
+    }
+    dq_equilibria(p, q, m, meq);
+    for (int i = 2; i < q; ++i) m[i] = (1.0 - p->s[i - 2]) * m[i] + p->s[i - 2] * meq[i];
+    for (int h = 0; h < q; ++h) {
+        double acc = 0.0;
+        for (int i = 0; i < q; ++i) acc = acc + Mi[h][i] * m[i];
+        f[h * stride] = acc;
+    }
+}
+
 /* Collision (Section 2.1.1; eq. LeavesCollision on a leaf): m = M f with
  * M = [[1, 1], [lambda, -lambda]] per field, relax the non-conserved moment,
  * f* = M^{-1} m*.  f holds the q populations of one cell with stride `stride`. */
 static void collide_cell(const orc_params *p, double *f, long stride) {
+    if (is_dq(p->eq)) {
+        dq_collide(p, f, stride);
+        return;
+    }
     int nf = orc_nfields(p->eq);
     double mc[ORC_MAXFIELDS], mn[ORC_MAXFIELDS], meq[ORC_MAXFIELDS];
     for (int i = 0; i < nf; ++i) {
@@ -248,6 +347,22 @@ static void collide_cell(const orc_params *p, double *f, long stride) {
 }
 
 void orc_equilibrium_populations(const orc_params *p, const double *m_cons, double *f, long n) {
+    if (is_dq(p->eq)) {
+        int q = orc_npop(p->eq);
+        double M[5][5], Mi[5][5], m[5];
+        dq_matrices(p, q, M, Mi);
+        for (long k = 0; k < n; ++k) {
+            m[0] = m_cons[k];
+            m[1] = m_cons[n + k];
+            dq_equilibria(p, q, m, m);
+            for (int h = 0; h < q; ++h) {
+                double acc = 0.0;
+                for (int i = 0; i < q; ++i) acc = acc + Mi[h][i] * m[i];
+                f[h * n + k] = acc;
+            }
+        }
+        return;
+    }
     int nf = orc_nfields(p->eq);
     for (long k = 0; k < n; ++k) {
         double mc[ORC_MAXFIELDS], meq[ORC_MAXFIELDS];
@@ -262,6 +377,19 @@ void orc_equilibrium_populations(const orc_params *p, const double *m_cons, doub
 }
 
 void orc_moments(const orc_params *p, const double *f, double *m_cons, long n) {
+    if (is_dq(p->eq)) {
+        int w[ORC_MAXQ], q = velocities(p->eq, w);
+        for (long k = 0; k < n; ++k) {
+            double m0 = 0.0, m1 = 0.0;
+            for (int h = 0; h < q; ++h) {
+                m0 = m0 + f[h * n + k];
+                m1 = m1 + (w[h] * p->lambda) * f[h * n + k];
+            }
+            m_cons[k] = m0;
+            m_cons[n + k] = m1;
+        }
+        return;
+    }
     int nf = orc_nfields(p->eq);
     for (long k = 0; k < n; ++k)
         for (int i = 0; i < nf; ++i) m_cons[i * n + k] = f[(2 * i) * n + k] + f[(2 * i + 1) * n + k];
@@ -271,11 +399,11 @@ void orc_moments(const orc_params *p, const double *f, double *m_cons, long n) {
  * then f^{n+1}_k = f*_{k - w^h} (Section 2.1.2). */
 void orc_uniform_step(const orc_params *p, double *f) {
     long n = ncells(p->Jmax);
-    int nf = orc_nfields(p->eq), q = 2 * nf;
+    int wv[ORC_MAXQ], q = velocities(p->eq, wv);
     for (long k = 0; k < n; ++k) collide_cell(p, f + k, n);
     double *row = (double *)malloc(sizeof(double) * n);
     for (int h = 0; h < q; ++h) {
-        int w = (h & 1) ? -1 : 1;
+        int w = wv[h];
         memcpy(row, f + (long)h * n, sizeof(double) * n);
         for (long k = 0; k < n; ++k) f[(long)h * n + k] = row[wrap_or_clamp(p->bc, k - w, n)];
     }
@@ -291,8 +419,7 @@ orc_state *orc_create(const orc_params *p) {
     orc_state *st = (orc_state *)calloc(1, sizeof(orc_state));
     st->p = *p;
     st->nf = orc_nfields(p->eq);
-    st->q = 2 * st->nf;
-    for (int h = 0; h < st->q; ++h) st->w[h] = (h & 1) ? -1 : 1;
+    st->q = velocities(p->eq, st->w);
     level_offsets(p->Jmin, p->Jmax, st->off);
     st->S = st->off[p->Jmax + 1];
     st->R = (unsigned char *)calloc(st->S, 1);
@@ -377,7 +504,8 @@ void orc_adapt(orc_state *st) {
     const orc_params *p = &st->p;
     double c[3];
     orc_prediction_coefficients(p->gamma, c);
-    int sigma = 1; /* max |w^h| of the D1Q2 fields */
+    int sigma = 1; /* enlargement width: max |w^h| of the scheme */
+    for (int h = 0; h < st->q; ++h) sigma = abs(st->w[h]) > sigma ? abs(st->w[h]) : sigma;
 
     /* multiresolution analysis of the current solution */
     fill_values(st, st->V);
@@ -533,9 +661,12 @@ void orc_mass(const orc_state *st, double *mass) {
     for (int l = st->p.Jmin; l <= st->p.Jmax; ++l) {
         double dx = ldexp(st->p.b - st->p.a, -l);
         for (long k = 0; k < ncells(l); ++k)
-            if (is_leaf(st, l, k))
-                for (int i = 0; i < st->nf; ++i)
-                    mass[i] += dx * (VAL(st, st->V, 2 * i, l, k) + VAL(st, st->V, 2 * i + 1, l, k));
+            if (is_leaf(st, l, k)) {
+                double f[ORC_MAXQ], m[ORC_MAXFIELDS];
+                for (int h = 0; h < st->q; ++h) f[h] = VAL(st, st->V, h, l, k);
+                orc_moments(&st->p, f, m, 1);
+                for (int i = 0; i < st->nf; ++i) mass[i] += dx * m[i];
+            }
     }
 }
 

@@ -33,6 +33,10 @@ extern "C" {
 #define ORC_EQ_BURGERS 1   /* n = 1, m1eq = m0^2 / 2             */
 #define ORC_EQ_SW 2        /* n = 2, shallow water, gravity g    */
 #define ORC_EQ_EULER 3     /* n = 3, Euler, gas constant gamma_g */
+/* shallow water with one velocity set for both conserved moments (Section 5.2):
+ * populations numbered as the paper's velocities, moments m^i = sum_h (v^h)^i f^h */
+#define ORC_EQ_SW_D1Q3 4   /* v = 0, +lambda, -lambda; s[0] = s^2 */
+#define ORC_EQ_SW_D1Q5 5   /* v = 0, +-lambda, +-2 lambda; s = (s^2, s^3, s^4), alpha = beta = 1 */
 
 typedef struct {
     int Jmin, Jmax; /* levels, Jmin >= 1 */
@@ -43,7 +47,8 @@ typedef struct {
     double a, b;    /* domain [a, b] */
     int eq;         /* ORC_EQ_* */
     double lambda;  /* lattice velocity */
-    double s[ORC_MAXFIELDS];   /* relaxation rate of the non-conserved moment of each field */
+    double s[ORC_MAXFIELDS];   /* relaxation rate of the non-conserved moment of each field
+                                  (D1Q3 / D1Q5: of the moments m^2, m^3, m^4) */
     double eqp;     /* advection velocity c | unused | gravity g | gas constant gamma_g */
 } orc_params;
 
@@ -51,6 +56,8 @@ typedef struct orc_state orc_state;
 
 /* number of D1Q2 fields (conserved moments) and populations of a scheme */
 int orc_nfields(int eq);
+/* number of populations q of the scheme */
+int orc_npop(int eq);
 
 orc_state *orc_create(const orc_params *p);
 void orc_free(orc_state *st);

@@ -19,6 +19,8 @@ Jmax = 9 and unstated boundary conditions):
   batch      4096 seeded instances mixing the four families, Jmax in 8..14,
              eps log-uniform in [1e-5, 1e-2], piecewise-constant data with
              1..6 jumps, periodic.
+  sw_d1q3/5  shallow water dam break with the D1Q3 / D1Q5 schemes (Section 5.2):
+             (h, u) = (2, 0) | (1, 0), lambda 2, g 1, T 0.2, Jmax 9, copy boundary.
   test1..4   the scalar D1Q2 test cases I-IV of Table 1 (Section 5.1):
              Omega = [-3, 3], lambda = 1, Jmin 2, Jmax 9, gamma 1, eps 1e-4,
              with their exact solutions (scalar_test, scalar_exact).
@@ -31,7 +33,9 @@ from dataclasses import dataclass, field, replace
 import numpy as np
 
 EQ_ADVECTION, EQ_BURGERS, EQ_SW, EQ_EULER = 0, 1, 2, 3
-NFIELDS = {EQ_ADVECTION: 1, EQ_BURGERS: 1, EQ_SW: 2, EQ_EULER: 3}
+EQ_SW_D1Q3, EQ_SW_D1Q5 = 4, 5  # shallow water on one velocity set (Section 5.2)
+NFIELDS = {EQ_ADVECTION: 1, EQ_BURGERS: 1, EQ_SW: 2, EQ_EULER: 3, EQ_SW_D1Q3: 2, EQ_SW_D1Q5: 2}
+NPOP = {EQ_ADVECTION: 2, EQ_BURGERS: 2, EQ_SW: 4, EQ_EULER: 6, EQ_SW_D1Q3: 3, EQ_SW_D1Q5: 5}
 BC_PERIODIC, BC_COPY = 0, 1
 GAMMA_GAS = 1.4
 
@@ -53,7 +57,7 @@ class Instance:
     gamma: int = 1
     mu_bar: int = 0
     s: tuple = (1.0, 1.0, 1.0)
-    eqp: float = 0.0  # advection velocity | unused | gravity | gas constant
+    eqp: float = 0.0  # advection velocity | unused | gravity | gas constant | gravity (D1Q3, D1Q5)
     m0: np.ndarray = field(default=None, repr=False)  # (nf, 2^Jmax) cell averages
 
     @property
@@ -62,7 +66,7 @@ class Instance:
 
     @property
     def q(self) -> int:
-        return 2 * self.nf
+        return NPOP[self.eq]
 
     @property
     def dx(self) -> float:
@@ -196,12 +200,12 @@ def random_smooth(Jmax: int, eq: int, seed: int, Jmin: int = 2, eps: float = 1e-
                   nmodes: int = 3) -> Instance:
     """Small seeded instance with smooth plus step data, for parity tests."""
     rng = np.random.Generator(np.random.PCG64(seed))
-    lam = {EQ_ADVECTION: 1.0, EQ_BURGERS: 1.0, EQ_SW: 2.0, EQ_EULER: 3.0}[eq]
+    lam = {EQ_ADVECTION: 1.0, EQ_BURGERS: 1.0, EQ_SW: 2.0, EQ_EULER: 3.0, EQ_SW_D1Q3: 2.0, EQ_SW_D1Q5: 3.0}[eq]
     nf = NFIELDS[eq]
     inst = Instance(f"rand{seed}", eq, Jmin, Jmax, eps, lam, -1.0, 1.0, bc, 0.0,
                     s=tuple(float(v) for v in rng.uniform(0.8, 1.6, 3)),
                     eqp={EQ_ADVECTION: float(rng.uniform(-0.9, 0.9)), EQ_BURGERS: 0.0,
-                         EQ_SW: 1.0, EQ_EULER: GAMMA_GAS}[eq])
+                         EQ_SW: 1.0, EQ_EULER: GAMMA_GAS, EQ_SW_D1Q3: 1.0, EQ_SW_D1Q5: 1.0}[eq])
     e = cell_edges(-1.0, 1.0, Jmax)
     xs = float(rng.uniform(-0.5, 0.5))
     base = avg_indicator(e, -1.0, xs)
@@ -211,7 +215,7 @@ def random_smooth(Jmax: int, eq: int, seed: int, Jmin: int = 2, eps: float = 1e-
                                      float(rng.uniform(0.03, 0.2)))
     if eq in (EQ_ADVECTION, EQ_BURGERS):
         inst.m0 = (0.5 * base + bumps - 0.2)[None, :]
-    elif eq == EQ_SW:
+    elif eq in (EQ_SW, EQ_SW_D1Q3, EQ_SW_D1Q5):
         h = 1.0 + 0.8 * base + bumps
         inst.m0 = np.stack([h, 0.1 * bumps])
     else:
@@ -219,6 +223,58 @@ def random_smooth(Jmax: int, eq: int, seed: int, Jmin: int = 2, eps: float = 1e-
         p = 0.3 + 0.5 * base
         inst.m0 = np.stack([rho, 0.05 * bumps, p / (GAMMA_GAS - 1.0)])
     return inst
+
+
+# shallow water with the D1Q3 / D1Q5 schemes (Section 5.2) ---------------------
+
+def shallow_water_dq(scheme: str = "d1q3", Jmax: int = 9, eps: float = 1e-4, s2: float = 1.5, T: float = 0.2,
+                     Jmin: int = 2) -> Instance:
+    """Section 5.2: Riemann datum (h, u) = (2, 0) for x < 0, (1, 0) for x > 0 on
+    [-1, 1], lambda = 2, g = 1, T = 0.2; relaxation s^2 (D1Q5: s^3 = s^4 = 1,
+    alpha = beta = 1); copy boundary (no wave reaches it before T)."""
+    eq = {"d1q3": EQ_SW_D1Q3, "d1q5": EQ_SW_D1Q5}[scheme]
+    inst = Instance(f"sw_{scheme}", eq, Jmin, Jmax, eps, 2.0, -1.0, 1.0, BC_COPY, T,
+                    s=(s2,) if eq == EQ_SW_D1Q3 else (s2, 1.0, 1.0), eqp=1.0)
+    e = cell_edges(inst.a, inst.b, Jmax)
+    h = 2.0 * avg_indicator(e, -1.0, 0.0) + 1.0 * avg_indicator(e, 0.0, 1.0)
+    inst.m0 = np.stack([h, np.zeros_like(h)])
+    return inst
+
+
+def sw_riemann_exact(edges: np.ndarray, t: float, hl: float = 2.0, hr: float = 1.0, g: float = 1.0,
+                     sub: int = 64) -> np.ndarray:
+    """Cell averages of (h, h u) of the exact entropy solution of the shallow
+    water Riemann problem with u = 0 on both sides and hl > hr (rarefaction to
+    the left, shock to the right); the averages are midpoint sums over `sub`
+    points per cell (the solution is piecewise smooth)."""
+    cl, cr = math.sqrt(g * hl), math.sqrt(g * hr)
+
+    def fL(h):  # rarefaction branch, h < hl
+        return 2.0 * (math.sqrt(g * h) - cl)
+
+    def fR(h):  # shock branch, h > hr
+        return (h - hr) * math.sqrt(0.5 * g * (h + hr) / (h * hr))
+
+    lo, hi = hr, hl
+    for _ in range(200):  # fL + fR increasing in h; root between hr and hl
+        mid = 0.5 * (lo + hi)
+        if fL(mid) + fR(mid) < 0.0:
+            lo = mid
+        else:
+            hi = mid
+    hs = 0.5 * (lo + hi)
+    us = -fL(hs)
+    cs = math.sqrt(g * hs)
+    S = hs * us / (hs - hr)  # Rankine-Hugoniot speed of the shock
+    x = np.asarray(edges, dtype=np.float64)
+    n = x.size - 1
+    pts = x[:-1, None] + (np.arange(sub)[None, :] + 0.5) / sub * np.diff(x)[:, None]
+    xi = pts / t
+    h = np.where(xi < -cl, hl, np.where(xi < us - cs, ((2.0 * cl - xi) / 3.0) ** 2 / g,
+                                        np.where(xi < S, hs, hr)))
+    u = np.where(xi < -cl, 0.0, np.where(xi < us - cs, (2.0 * cl + 2.0 * xi) / 3.0,
+                                         np.where(xi < S, us, 0.0)))
+    return np.stack([h.mean(axis=1), (h * u).mean(axis=1)]).reshape(2, n)
 
 
 # the scalar test cases of Table 1 (Section 5.1) ------------------------------
@@ -314,4 +370,6 @@ WORKLOADS = {
     "test2": lambda: scalar_test("II"),
     "test3": lambda: scalar_test("III"),
     "test4": lambda: scalar_test("IV"),
+    "sw_d1q3": lambda: shallow_water_dq("d1q3"),
+    "sw_d1q5": lambda: shallow_water_dq("d1q5"),
 }
