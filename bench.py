@@ -325,8 +325,8 @@ def accuracy_scalar(inst, name: str):
     from paper_2102_12163_gb300 import MR_FP32_MIXED, MR_FP64, MRLBM
     from paper_2102_12163_gb300 import workloads as W
 
-    test = {"test1": "I", "test2": "II", "test3": "III", "test4": "IV"}[name]
-    table2_s1 = {"I": 59.4, "II": 2310.0, "III": 37.1, "IV": 341.0}[test]
+    test = {"test1": "I", "test2": "II", "test3": "III", "test4": "IV", "sw_d1q3": "SW", "sw_d1q5": "SW"}[name]
+    table2_s1 = {"I": 59.4, "II": 2310.0, "III": 37.1, "IV": 341.0}.get(test)
     N = inst.nsteps
 
     def run(prec, eps):
@@ -335,18 +335,23 @@ def accuracy_scalar(inst, name: str):
         s.set_initial()
         s.advance(N)
         s.sync()
-        out, nl = s.finest()[0], len(s.leaves()[0])
+        out, nl = s.finest(), len(s.leaves()[0])
         s.close()
         return out, nl
 
-    M, _ = run(MR_FP64, 0.0)
-    exact = W.scalar_exact(test, W.cell_edges(inst.a, inst.b, inst.Jmax), N * inst.dx / inst.lam)
+    edges = W.cell_edges(inst.a, inst.b, inst.Jmax)
+    if test == "SW":  # dam break of Section 5.2: both conserved moments (h, hu)
+        M, _ = run(MR_FP64, 0.0)
+        exact = W.sw_riemann_exact(edges, N * inst.dx / inst.lam)
+    else:
+        M, _ = run(MR_FP64, 0.0)
+        M, exact = M[:1], W.scalar_exact(test, edges, N * inst.dx / inst.lam)[None, :]
     E = float(inst.dx * np.abs(exact - M).sum())
-    out = {"test": test, "s": inst.s[0], "steps": N, "E_reference_vs_exact": E,
-           "table2_E_over_delta_at_s1": table2_s1}
+    out = {"test": test if test != "SW" else f"dam break, {name[3:].upper()}", "s": inst.s[0], "steps": N,
+           "E_reference_vs_exact": E, "table2_E_over_delta_at_s1": table2_s1}
     for key, prec in (("fp64", MR_FP64), ("fp32", MR_FP32_MIXED)):
         f, nl = run(prec, inst.eps)
-        d = float(inst.dx * np.abs(M - f).sum())
+        d = float(inst.dx * np.abs(M - f[: M.shape[0]]).sum())
         out[key] = {"delta": d, "E_over_delta": E / d if d > 0 else None,
                     "compression_percent": 100.0 * (1.0 - nl / (1 << inst.Jmax))}
     return out
@@ -362,7 +367,8 @@ def main():
     ap.add_argument("--instances", type=int, default=4096, help="batch size (smaller only for profiling)")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="batch",
-                    choices=["batch", "advection", "burgers", "shallow", "sod", "test1", "test2", "test3", "test4"])
+                    choices=["batch", "advection", "burgers", "shallow", "sod", "test1", "test2", "test3", "test4",
+                             "sw_d1q3", "sw_d1q5"])
     ap.add_argument("--block", type=int, default=None)
     ap.add_argument("--gamma", type=int, default=1, choices=[1, 2, 3],
                     help="prediction stencil half-width of every instance (Section 3.1)")
@@ -428,7 +434,7 @@ def main():
     acc = None
     if rank == 0 and not args.no_accuracy and args.workload == "batch":
         acc = accuracy(insts, min(args.steps, 64))
-    elif rank == 0 and not args.no_accuracy and args.workload.startswith("test"):
+    elif rank == 0 and not args.no_accuracy and (args.workload.startswith("test") or args.workload.startswith("sw_")):
         acc = accuracy_scalar(insts[0], args.workload)
 
     cpu = None

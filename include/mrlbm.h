@@ -59,8 +59,20 @@ typedef enum { MR_BC_PERIODIC = 0, MR_BC_COPY = 1 } mr_bc;
  *   ADVECTION   n = 1, m1eq = c m0                         eq_param = c
  *   BURGERS     n = 1, m1eq = m0^2 / 2                     eq_param unused
  *   SW_VEC      n = 2, shallow water (h, hu), gravity g    eq_param = g
- *   EULER_VEC   n = 3, Euler (rho, rho u, E), Section 5.3  eq_param = gamma_gas */
-typedef enum { MR_EQ_ADVECTION = 0, MR_EQ_BURGERS = 1, MR_EQ_SW_VEC = 2, MR_EQ_EULER_VEC = 3 } mr_equilibrium;
+ *   EULER_VEC   n = 3, Euler (rho, rho u, E), Section 5.3  eq_param = gamma_gas
+ * and of the shallow water schemes on one velocity set (Section 5.2), two
+ * conserved moments (h, hu), populations in the order of the velocities:
+ *   SW_D1Q3     q = 3, v = (0, lambda, -lambda), relaxed m^2 with s[0];
+ *               m^{2,eq} = (hu)^2 / h + g h^2 / 2          eq_param = g
+ *   SW_D1Q5     q = 5, v = (0, +-lambda, +-2 lambda), relaxed m^2, m^3, m^4
+ *               with s[0..2]; m^{3,eq} = lambda^2 hu, m^{4,eq} = lambda^2
+ *               m^{2,eq} (alpha = beta = 1), enlargement width sigma = 2;
+ *               eq_param = g
+ * (moments m^i = sum_h (v^h)^i f^h).  D1Q3 / D1Q5 need gamma = 1. */
+typedef enum {
+    MR_EQ_ADVECTION = 0, MR_EQ_BURGERS = 1, MR_EQ_SW_VEC = 2, MR_EQ_EULER_VEC = 3,
+    MR_EQ_SW_D1Q3 = 4, MR_EQ_SW_D1Q5 = 5
+} mr_equilibrium;
 
 /* Per-instance description for the batched interface. */
 typedef struct {

@@ -18,7 +18,8 @@ from .capi import MR_FP32_MIXED, MR_FP64, MRError
 __all__ = ["MRLBM", "MRError", "capi", "workloads", "MR_FP64", "MR_FP32_MIXED"]
 
 _EQ = {workloads.EQ_ADVECTION: capi.MR_EQ_ADVECTION, workloads.EQ_BURGERS: capi.MR_EQ_BURGERS,
-       workloads.EQ_SW: capi.MR_EQ_SW_VEC, workloads.EQ_EULER: capi.MR_EQ_EULER_VEC}
+       workloads.EQ_SW: capi.MR_EQ_SW_VEC, workloads.EQ_EULER: capi.MR_EQ_EULER_VEC,
+       workloads.EQ_SW_D1Q3: capi.MR_EQ_SW_D1Q3, workloads.EQ_SW_D1Q5: capi.MR_EQ_SW_D1Q5}
 
 
 def _desc(inst: "workloads.Instance") -> capi.mr_instance_desc:

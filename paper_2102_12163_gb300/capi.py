@@ -14,6 +14,7 @@ MR_OK, MR_ERR_ARG, MR_ERR_CUDA, MR_ERR_CAPACITY, MR_ERR_NONFINITE, MR_ERR_TIMEOU
 MR_FP64, MR_FP32_MIXED = 0, 1
 MR_BC_PERIODIC, MR_BC_COPY = 0, 1
 MR_EQ_ADVECTION, MR_EQ_BURGERS, MR_EQ_SW_VEC, MR_EQ_EULER_VEC = 0, 1, 2, 3
+MR_EQ_SW_D1Q3, MR_EQ_SW_D1Q5 = 4, 5
 
 STATUS_NAMES = {0: "MR_OK", -1: "MR_ERR_ARG", -2: "MR_ERR_CUDA", -3: "MR_ERR_CAPACITY",
                 -4: "MR_ERR_NONFINITE", -5: "MR_ERR_TIMEOUT", -6: "MR_ERR_STATE"}

@@ -30,11 +30,50 @@ int nfields_of(int eq) {
     case MR_EQ_BURGERS: return 1;
     case MR_EQ_SW_VEC: return 2;
     case MR_EQ_EULER_VEC: return 3;
+    case MR_EQ_SW_D1Q3:
+    case MR_EQ_SW_D1Q5: return 2;
     default: return 0;
     }
 }
+// populations q and relaxation rates of a scheme
+int npop_of(int eq) { return eq == MR_EQ_SW_D1Q3 ? 3 : eq == MR_EQ_SW_D1Q5 ? 5 : 2 * nfields_of(eq); }
+int nrates_of(int eq) { return eq == MR_EQ_SW_D1Q3 ? 1 : eq == MR_EQ_SW_D1Q5 ? 3 : nfields_of(eq); }
+
+// D1Q3 / D1Q5: inverse of the moment matrix M[i][h] = (v^h)^i, v = lambda (0, 1, -1, 2, -2),
+// by Gauss-Jordan elimination with partial pivoting
+void dq_inverse(int eq, double lambda, double inv[5][5]) {
+    const int q = npop_of(eq);
+    const double w[5] = {0.0, 1.0, -1.0, 2.0, -2.0};
+    double A[5][10];
+    for (int i = 0; i < 5; ++i)
+        for (int j = 0; j < 5; ++j) inv[i][j] = 0.0;
+    for (int i = 0; i < q; ++i)
+        for (int h = 0; h < q; ++h) {
+            double x = 1.0;
+            for (int e = 0; e < i; ++e) x *= w[h] * lambda;
+            A[i][h] = x;
+            A[i][q + h] = i == h ? 1.0 : 0.0;
+        }
+    for (int col = 0; col < q; ++col) {
+        int piv = col;
+        for (int r = col + 1; r < q; ++r)
+            if (std::fabs(A[r][col]) > std::fabs(A[piv][col])) piv = r;
+        for (int j = 0; j < 2 * q; ++j) std::swap(A[col][j], A[piv][j]);
+        const double dv = A[col][col];
+        for (int j = 0; j < 2 * q; ++j) A[col][j] /= dv;
+        for (int r = 0; r < q; ++r)
+            if (r != col) {
+                const double f = A[r][col];
+                for (int j = 0; j < 2 * q; ++j) A[r][j] -= f * A[col][j];
+            }
+    }
+    for (int i = 0; i < q; ++i)
+        for (int j = 0; j < q; ++j) inv[i][j] = A[i][q + j];
+}
 
 int nwords_h(int l) { return l >= 5 ? (1 << (l - 5)) : 1; }
+// compiled scheme variant of the kernels: D1Q2^n by field count, D1Q3, D1Q5
+int variant_of(int eq) { return eq == MR_EQ_SW_D1Q3 ? 4 : eq == MR_EQ_SW_D1Q5 ? 5 : nfields_of(eq); }
 
 thread_local std::string g_create_error;
 
@@ -95,8 +134,10 @@ static int check_desc(mr_ctx *c, const mr_instance_desc &d, int i) {
     if (nfields_of(d.eq) == 0) return c->fail(MR_ERR_ARG, "instance %d: bad equilibrium", i);
     if (!(d.eps >= 0.0) || !(d.b > d.a) || !(d.lambda > 0.0))
         return c->fail(MR_ERR_ARG, "instance %d: need eps >= 0, b > a, lambda > 0", i);
-    for (int j = 0; j < nfields_of(d.eq); ++j)
+    for (int j = 0; j < nrates_of(d.eq); ++j)
         if (!(d.s[j] > 0.0 && d.s[j] <= 2.0)) return c->fail(MR_ERR_ARG, "instance %d: relaxation rate outside (0, 2]", i);
+    if ((d.eq == MR_EQ_SW_D1Q3 || d.eq == MR_EQ_SW_D1Q5) && d.gamma != 1)
+        return c->fail(MR_ERR_ARG, "instance %d: the D1Q3 / D1Q5 schemes are built with gamma = 1", i);
     return MR_OK;
 }
 
@@ -129,7 +170,7 @@ static void layout(mr_ctx *c) {
     for (int i = 0; i < n; ++i) {
         const mr_instance_desc &d = c->desc[i];
         InstDesc &h = c->hdesc[i];
-        int nf = nfields_of(d.eq), q = 2 * nf;
+        int nf = nfields_of(d.eq), q = npop_of(d.eq);
         long long S = (1LL << (d.Jmax + 1)) - (1LL << d.Jmin), N = 1LL << d.Jmax;
         int W = 0;
         for (int l = d.Jmin; l <= d.Jmax; ++l) W += nwords_h(l);
@@ -138,6 +179,7 @@ static void layout(mr_ctx *c) {
         h.bc = d.bc;
         h.eq = d.eq;
         h.nf = nf;
+        if (d.eq == MR_EQ_SW_D1Q3 || d.eq == MR_EQ_SW_D1Q5) dq_inverse(d.eq, d.lambda, h.minv);
         h.mu_bar = d.mu_bar;
         h.gamma = d.gamma;
         h.Wtot = W;
@@ -183,28 +225,48 @@ static void make_tables(Tables<double> &td, Tables<float> &tf) {
     typedef __int128 i128;
     const i128 A[4][4] = {{1, 8, -1, 0}, {-1, 8, 1, 0}, {0, 1, 8, -1}, {0, -1, 8, 1}};
     const i128 B[2][2] = {{9, -1}, {7, 1}};
-    i128 v[4] = {0, 0, 1, 0}, u[2] = {1, 0};
+    // first cell: window position 2 (the cell p itself, even children all the way);
+    // second cell (v2, u2): window position 3, the odd child at the last level
+    i128 v[4] = {0, 0, 1, 0}, u[2] = {1, 0}, v2[4] = {0, 0, 0, 1}, u2[2] = {0, 1};
     std::memset(&td, 0, sizeof td);
     std::memset(&tf, 0, sizeof tf);
     for (int dj = 0; dj <= MAXDJ; ++dj) {
         for (int j = 0; j < 4; ++j) td.cf[dj][j] = std::ldexp((double)v[j], -3 * dj);
         for (int j = 0; j < 2; ++j) td.bf[dj][j] = std::ldexp((double)u[j], -3 * dj);
+        for (int j = 0; j < 4; ++j) td.cf2[dj][j] = std::ldexp((double)v2[j], -3 * dj);
+        for (int j = 0; j < 2; ++j) td.bf2[dj][j] = std::ldexp((double)u2[j], -3 * dj);
         if (dj > 0)
-            for (int j = 0; j < 4; ++j) td.t1[dj][j] = td.cf[dj - 1][j];
-        i128 nv[4] = {0, 0, 0, 0}, nu[2] = {0, 0};
+            for (int j = 0; j < 4; ++j) {
+                td.t1[dj][j] = td.cf[dj - 1][j];
+                td.t12[dj][j] = td.cf2[dj - 1][j];
+            }
+        i128 nv[4] = {0, 0, 0, 0}, nu[2] = {0, 0}, nv2[4] = {0, 0, 0, 0}, nu2[2] = {0, 0};
         for (int r = 0; r < 4; ++r)
-            for (int j = 0; j < 4; ++j) nv[j] += v[r] * A[r][j];
+            for (int j = 0; j < 4; ++j) {
+                nv[j] += v[r] * A[r][j];
+                nv2[j] += v2[r] * A[r][j];
+            }
         for (int r = 0; r < 2; ++r)
-            for (int j = 0; j < 2; ++j) nu[j] += u[r] * B[r][j];
+            for (int j = 0; j < 2; ++j) {
+                nu[j] += u[r] * B[r][j];
+                nu2[j] += u2[r] * B[r][j];
+            }
         std::memcpy(v, nv, sizeof v);
         std::memcpy(u, nu, sizeof u);
+        std::memcpy(v2, nv2, sizeof v2);
+        std::memcpy(u2, nu2, sizeof u2);
     }
     for (int dj = 0; dj <= MAXDJ; ++dj) {
         for (int j = 0; j < 4; ++j) {
             tf.cf[dj][j] = (float)td.cf[dj][j];
             tf.t1[dj][j] = (float)td.t1[dj][j];
+            tf.cf2[dj][j] = (float)td.cf2[dj][j];
+            tf.t12[dj][j] = (float)td.t12[dj][j];
         }
-        for (int j = 0; j < 2; ++j) tf.bf[dj][j] = (float)td.bf[dj][j];
+        for (int j = 0; j < 2; ++j) {
+            tf.bf[dj][j] = (float)td.bf[dj][j];
+            tf.bf2[dj][j] = (float)td.bf2[dj][j];
+        }
     }
     // prediction coefficients c_1..c_gamma (Section 3.1; gamma = 3 with c_3 = -5/1024,
     // the sign that makes the stencil exact on polynomials of degree 5); all dyadic
@@ -318,14 +380,16 @@ mr_status lbm_scheme(mr_ctx *c, int d, int q, double lambda, const double *s, in
     if (c->bound) return (mr_status)c->fail(MR_ERR_STATE, "lbm_scheme after mr_bind");
     if (d != 1) return (mr_status)c->fail(MR_ERR_ARG, "only D = 1 is built");
     int nf = nfields_of(eq);
-    if (nf == 0 || q != 2 * nf) return (mr_status)c->fail(MR_ERR_ARG, "equilibrium %d needs q = %d (got %d)", eq, 2 * nf, q);
+    if (nf == 0 || q != npop_of(eq))
+        return (mr_status)c->fail(MR_ERR_ARG, "equilibrium %d needs q = %d (got %d)", eq, npop_of(eq), q);
     if (!s) return (mr_status)c->fail(MR_ERR_ARG, "relaxation rates missing");
     mr_instance_desc dd = c->desc[0];
     dd.eq = eq;
     dd.lambda = lambda;
-    for (int j = 0; j < 3; ++j) dd.s[j] = j < nf ? s[j] : 1.0;
+    for (int j = 0; j < 3; ++j) dd.s[j] = j < nrates_of(eq) ? s[j] : 1.0;
     dd.eq_param = eq_params ? eq_params[0] : 0.0;
-    if ((eq == MR_EQ_ADVECTION || eq == MR_EQ_SW_VEC || eq == MR_EQ_EULER_VEC) && !eq_params)
+    if ((eq == MR_EQ_ADVECTION || eq == MR_EQ_SW_VEC || eq == MR_EQ_EULER_VEC || eq == MR_EQ_SW_D1Q3 ||
+         eq == MR_EQ_SW_D1Q5) && !eq_params)
         return (mr_status)c->fail(MR_ERR_ARG, "equilibrium parameter missing");
     int rc = check_desc(c, dd, 0);
     if (rc) return (mr_status)rc;
@@ -395,9 +459,10 @@ static int upload_order(mr_ctx *c) {
     for (int i = 0; i < n; ++i) order[i] = i;
     std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
         if ((dd[x].gamma > 1) != (dd[y].gamma > 1)) return dd[x].gamma == 1;  // kernel variant groups
-        if (c->order_by_fields && dd[x].nf != dd[y].nf) return dd[x].nf > dd[y].nf;
-        double cx = (double)dd[x].nf * std::ldexp(1.0, dd[x].Jmax);
-        double cy = (double)dd[y].nf * std::ldexp(1.0, dd[y].Jmax);
+        const int vx = variant_of(dd[x].eq), vy = variant_of(dd[y].eq);
+        if (c->order_by_fields && vx != vy) return vx > vy;
+        double cx = (double)npop_of(dd[x].eq) * std::ldexp(1.0, dd[x].Jmax);
+        double cy = (double)npop_of(dd[y].eq) * std::ldexp(1.0, dd[y].Jmax);
         return cx > cy;
     });
     c->order_host = order;
@@ -559,7 +624,7 @@ static int fetch_leaves(mr_ctx *c, int inst, std::vector<uint32_t> &ent, std::ve
     if (rc) return rc;
     if (st.status & ST_NONFINITE) return c->fail(MR_ERR_NONFINITE, "instance %d: non-finite population", inst);
     const InstDesc &h = c->hdesc[inst];
-    int q = 2 * h.nf;
+    int q = npop_of(h.eq);
     ent.resize(st.nleaf);
     if (st.nleaf)
         if ((rc = c->cuda(cudaMemcpy(ent.data(), h.lists + h.list_off[L_LEAF], sizeof(uint32_t) * st.nleaf, cudaMemcpyDeviceToHost), "copy")))
@@ -587,7 +652,7 @@ mr_status mr_get_leaves(mr_ctx *c, int inst, int *level, long *index, double *f,
     if (count) *count = st.nleaf;
     if ((level || index || f) && cap < st.nleaf) return (mr_status)c->fail(MR_ERR_CAPACITY, "need %d leaf slots", st.nleaf);
     const InstDesc &h = c->hdesc[inst];
-    int q = 2 * h.nf;
+    int q = npop_of(h.eq);
     for (int i = 0; i < st.nleaf; ++i) {
         int l = (int)(ent[i] >> KBITS);
         long k = (long)(ent[i] & KMASK);
@@ -616,8 +681,20 @@ mr_status mr_get_moments(mr_ctx *c, int inst, double *m, long cap, long *count) 
         for (int i = 0; i < st.nleaf; ++i) {
             int l = (int)(ent[i] >> KBITS);
             long long cell = ((1LL << l) - (1LL << h.Jmin)) + (ent[i] & KMASK);
-            for (int j = 0; j < h.nf; ++j)
-                m[(long)j * cap + i] = vals[(size_t)(2 * j) * h.S + cell] + vals[(size_t)(2 * j + 1) * h.S + cell];
+            if (h.eq == MR_EQ_SW_D1Q3 || h.eq == MR_EQ_SW_D1Q5) {
+                const double w[5] = {0.0, 1.0, -1.0, 2.0, -2.0};
+                double m0 = 0.0, m1 = 0.0;
+                for (int hh = 0; hh < npop_of(h.eq); ++hh) {
+                    const double f = vals[(size_t)hh * h.S + cell];
+                    m0 += f;
+                    m1 += (w[hh] * h.lam) * f;
+                }
+                m[i] = m0;
+                m[(long)cap + i] = m1;
+            } else {
+                for (int j = 0; j < h.nf; ++j)
+                    m[(long)j * cap + i] = vals[(size_t)(2 * j) * h.S + cell] + vals[(size_t)(2 * j + 1) * h.S + cell];
+            }
         }
     return MR_OK;
 }
@@ -836,6 +913,10 @@ mr_status mr_destroy(mr_ctx *c) {
 
 // Reconstruction tables for other translation units of the library.
 void mrg_tables(Tables<double> *td, Tables<float> *tf) { make_tables(*td, *tf); }
+int mrg_nfields(int eq) { return nfields_of(eq); }
+int mrg_npop(int eq) { return npop_of(eq); }
+int mrg_nrates(int eq) { return nrates_of(eq); }
+void mrg_dq_inverse(int eq, double lambda, double inv[5][5]) { dq_inverse(eq, lambda, inv); }
 
 // Message reported by mr_last_error(NULL, ...) for calls without a context.
 void mrg_set_error(const char *msg) { g_create_error = msg ? msg : ""; }

@@ -272,6 +272,67 @@ __device__ __forceinline__ void equilibrium_populations(const InstDesc &d, const
     }
 }
 
+// ---- shallow water on one velocity set (Section 5.2): D1Q3 (Q = 3), D1Q5 (Q = 5)
+// velocities v^h = lambda w^h, w = (0, 1, -1, 2, -2); moments m^i = sum_h (v^h)^i f^h
+__device__ __forceinline__ int dq_w(int h) { return h == 0 ? 0 : (h & 1) ? (h + 1) / 2 : -(h / 2); }
+
+// collision: the relaxed moments i >= 2 move to (1 - s^i) m^i + s^i m^{i,eq}, with
+// m^{2,eq} = (hu)^2 / h + g h^2 / 2, m^{3,eq} = lambda^2 hu, m^{4,eq} = lambda^2
+// m^{2,eq}; f* = f + M^{-1} (m* - m) (the conserved rows of m* - m are zero)
+template <typename T, int Q>
+__device__ __forceinline__ void dq_collide(const InstDesc &d, T *f) {
+    const T lam = (T)d.lam;
+    T m[Q];
+#pragma unroll
+    for (int i = 0; i < Q; ++i) m[i] = T(0);
+#pragma unroll
+    for (int h = 0; h < Q; ++h) {
+        const T v = (T)dq_w(h) * lam;
+        T x = f[h];
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+            m[i] = m[i] + x;
+            x = x * v;
+        }
+    }
+    T meq[Q];
+    meq[2] = (m[1] * m[1]) / m[0] + (T(0.5) * (T)d.eqp) * (m[0] * m[0]);
+    if constexpr (Q == 5) {
+        meq[3] = (lam * lam) * m[1];
+        meq[4] = (lam * lam) * meq[2];
+    }
+    T dm[Q];
+#pragma unroll
+    for (int i = 2; i < Q; ++i) dm[i] = (T)d.s[i - 2] * (meq[i] - m[i]);
+#pragma unroll
+    for (int h = 0; h < Q; ++h) {
+        T acc = T(0);
+#pragma unroll
+        for (int i = 2; i < Q; ++i) acc = acc + (T)d.minv[h][i] * dm[i];
+        f[h] = f[h] + acc;
+    }
+}
+
+// populations at equilibrium of (h, hu), in FP64: f = M^{-1} (h, hu, m^{2,eq}, ...)
+template <int Q>
+__device__ __forceinline__ void dq_equilibrium_populations(const InstDesc &d, const double *mc, double *f) {
+    double m[5];
+    m[0] = mc[0];
+    m[1] = mc[1];
+    m[2] = (mc[1] * mc[1]) / mc[0] + (0.5 * d.eqp) * (mc[0] * mc[0]);
+    if constexpr (Q == 5) {
+        m[3] = (d.lam * d.lam) * mc[1];
+        m[4] = (d.lam * d.lam) * m[2];
+    }
+#pragma unroll
+    for (int h = 0; h < Q; ++h) {
+        double acc = 0.0;
+#pragma unroll
+        for (int i = 0; i < Q; ++i) acc = acc + d.minv[h][i] * m[i];
+        f[h] = acc;
+    }
+}
+
 // prediction of child `odd` of cell p of a row at level lp (Section 3.1, gamma = 1)
 template <typename T>
 __device__ __forceinline__ T predict(const T *row, long long p, int odd, int lp, int bc) {
@@ -377,7 +438,11 @@ constexpr int QMAX = 6;  // populations of the largest scheme (vectorial D1Q2^3)
 template <typename T, int NF, int TS, bool WIDE>
 struct Worker {
     static constexpr bool WARP = TS == 32;
-    static constexpr int nf = NF, q = 2 * NF;  // fields and populations of the scheme
+    // NF = 1, 2, 3: vectorial D1Q2^NF; NF = 4: D1Q3, NF = 5: D1Q5 shallow water
+    static constexpr bool DQ = NF >= 4;
+    static constexpr int nf = DQ ? 2 : NF;                          // conserved moments
+    static constexpr int q = DQ ? (NF == 4 ? 3 : 5) : 2 * NF;       // populations
+    static constexpr int SIGMA = NF == 5 ? 2 : 1;                   // enlargement width max |w^h|
     TeamSmem<T> &sm;
     const Tables<T> &tab;
     BlockScratch &bx;
@@ -395,7 +460,12 @@ struct Worker {
     }
 
     // leaves collision of the q populations of one cell
-    __device__ __forceinline__ void collide_cell(T *f) const { collide<T, NF>(d, f); }
+    __device__ __forceinline__ void collide_cell(T *f) const {
+        if constexpr (DQ)
+            dq_collide<T, q>(d, f);
+        else
+            collide<T, NF>(d, f);
+    }
 
     __device__ __forceinline__ void sync() const {
         if constexpr (WARP)
@@ -691,7 +761,7 @@ struct Worker {
             } else {
                 const uint32_t *kl = keep + sm.woff[l];
                 uint32_t rt = kl[wi];
-                rh = rt | pairexpand(dilate([&](int j) { return kl[j]; }, l, wi, 1, d.bc));
+                rh = rt | pairexpand(dilate([&](int j) { return kl[j]; }, l, wi, SIGMA, d.bc));
                 if (l >= d.Jmin + 2) rh |= spread16(ref[sm.woff[l - 1] + (wi >> 1)] >> (16 * (wi & 1)));
             }
             Rn[g] = rh & vb;
@@ -997,6 +1067,10 @@ struct Worker {
             reconstruct_wide();
             return;
         }
+        if constexpr (DQ) {
+            reconstruct_dq();
+            return;
+        }
         const uint32_t *R = mask(sm.cur);
         const uint32_t *leaves = list(L_LEAF);
         for (int i = tid; i < sm.nleaf; i += TS) {
@@ -1110,6 +1184,174 @@ struct Worker {
         }
     }
 
+    // S4 for the D1Q3 / D1Q5 schemes: every leaf writes the reconstructed
+    // finest values it holds within |w^h| cells of its edges, by finest
+    // position: a +v population needs the cells left of each interface (the
+    // last |w| cells of a leaf), a -v population the cells right of it (the
+    // first |w|); at a copy boundary also the cell next to the boundary, which
+    // the clamped out-of-domain cells copy.  Second cells from an edge use the
+    // second-cell tables.
+    __device__ __noinline__ void reconstruct_dq() {
+        const uint32_t *R = mask(sm.cur);
+        const uint32_t *leaves = list(L_LEAF);
+        for (int i = tid; i < sm.nleaf; i += TS) {
+            const uint32_t ent = leaves[i];
+            const int l = ent >> KBITS;
+            const long long k = ent & KMASK;
+            const int dj = d.Jmax - l;
+            const long long first = k << dj, last = ((k + 1) << dj) - 1;
+            const bool at_left = d.bc == 1 && k == 0, at_right = d.bc == 1 && k == (1LL << l) - 1;
+            bool fin_l = false, fin_r = false;
+            long long cl = 0, cr = 0;
+            if (dj > 0) {
+                const uint32_t *rf = R + sm.woff[l + 1];
+                cl = 2 * wrapc(k - 1, l, d.bc);
+                cr = 2 * wrapc(k + 1, l, d.bc);
+                if (!at_left) fin_l = (rf[cl >> 5] >> (cl & 31)) & 1u;
+                if (!at_right) fin_r = (rf[cr >> 5] >> (cr & 31)) & 1u;
+            }
+            for (int h = 1; h < q; ++h) {
+                const int w = dq_w(h), a = w < 0 ? -w : w;
+                const T *r = row(h, l);
+                T *ph = Phi + (long long)h * (d.N + 1);
+                if (dj == 0) {
+                    ph[first] = r[k];
+                    continue;
+                }
+                const T vm1 = r[wrapc(k - 1, l, d.bc)], v0 = r[k], vp1 = r[wrapc(k + 1, l, d.bc)];
+                const T tt = T(C1) * (vp1 - vm1);
+                const T pe = v0 + tt, po = v0 - tt;  // children of the leaf
+                const T *rf = row(h, l + 1);
+                // cell `sec` (0: first / last, 1: second from that edge) next to the left or right edge
+                auto from_left = [&](int sec) -> T {
+                    const T *bf = sec ? tab.bf2[dj] : tab.bf[dj], *t1 = sec ? tab.t12[dj] : tab.t1[dj],
+                            *cf = sec ? tab.cf2[dj] : tab.cf[dj];
+                    if (at_left) return bf[0] * v0 + bf[1] * vp1;
+                    if (fin_l) return dot4(t1[0], rf[cl], t1[1], rf[cl + 1], t1[2], pe, t1[3], po);
+                    return dot4(cf[0], r[wrapc(k - 2, l, d.bc)], cf[1], vm1, cf[2], v0, cf[3], vp1);
+                };
+                auto from_right = [&](int sec) -> T {
+                    const T *bf = sec ? tab.bf2[dj] : tab.bf[dj], *t1 = sec ? tab.t12[dj] : tab.t1[dj],
+                            *cf = sec ? tab.cf2[dj] : tab.cf[dj];
+                    if (at_right) return bf[0] * v0 + bf[1] * vm1;
+                    if (fin_r) return dot4(t1[3], pe, t1[2], po, t1[1], rf[cr], t1[0], rf[cr + 1]);
+                    return dot4(cf[3], vm1, cf[2], v0, cf[1], vp1, cf[0], r[wrapc(k + 2, l, d.bc)]);
+                };
+                if (w > 0) {
+                    ph[last] = from_right(0);
+                    if (a == 2) ph[last - 1] = from_right(1);
+                    if (at_left) ph[first] = from_left(0);
+                } else {
+                    ph[first] = from_left(0);
+                    if (a == 2) ph[first + 1] = from_left(1);
+                    if (at_right) ph[last] = from_right(0);
+                }
+            }
+        }
+    }
+
+    // S5 for the D1Q3 / D1Q5 schemes (eq. AdaptiveStreamPhase with |w| <= 2):
+    // f^{n+1} = f* + sigma 2^-dj sum_{delta=1}^{|w|} (V[first + eta] - V[next + eta]),
+    // eta = -delta (sigma > 0) or delta - 1 (sigma < 0), V the finest values of
+    // reconstruct_dq (wrapped, or clamped at a copy boundary); audit of (h, hu)
+    __device__ __noinline__ void stream_dq() {
+        const uint32_t *leaves = list(L_LEAF);
+        const long long N = d.N;
+        auto at = [&](long long i) -> long long { return d.bc == 0 ? (i & (N - 1)) : (i < 0 ? 0 : (i >= N ? N - 1 : i)); };
+        double macc[3] = {0.0, 0.0, 0.0};
+        float fhi[3] = {0.0f, 0.0f, 0.0f}, flo[3] = {0.0f, 0.0f, 0.0f};
+        bool bad = false;
+        for (int i = tid; i < sm.nleaf; i += TS) {
+            const uint32_t ent = leaves[i];
+            const int l = ent >> KBITS;
+            const long long k = ent & KMASK;
+            const int dj = d.Jmax - l;
+            const long long first = k << dj, next = (k + 1) << dj;
+            const T wgt = (T)ldexpf(1.0f, -dj);
+            T fn[QMAX];
+#pragma unroll
+            for (int h = 0; h < QMAX; ++h)
+                if (h < q) {
+                    const int w = dq_w(h);
+                    T *r = row(h, l);
+                    T v = r[k];
+                    if (w != 0) {
+                        const T *ph = Phi + (long long)h * (N + 1);
+                        const int a = w < 0 ? -w : w;
+                        T acc = T(0);
+                        for (int dl = 1; dl <= a; ++dl) {
+                            const long long eta = w > 0 ? -dl : dl - 1;
+                            acc = acc + (ph[at(first + eta)] - ph[at(next + eta)]);
+                        }
+                        v = v + (w > 0 ? wgt : -wgt) * acc;
+                    }
+                    bad |= !isfinite(v);
+                    r[k] = v;
+                    fn[h] = v;
+                }
+            if constexpr (sizeof(T) == 8) {
+                double m0 = 0.0, m1 = 0.0;
+#pragma unroll
+                for (int h = 0; h < QMAX; ++h)
+                    if (h < q) {
+                        m0 += (double)fn[h];
+                        m1 += (dq_w(h) * d.lam) * (double)fn[h];
+                    }
+                macc[0] += sm.dx_l[l] * m0;
+                macc[1] += sm.dx_l[l] * m1;
+            } else {
+                // exact per-leaf sums of f and of w f in float-float, scaled by 2^-l
+                const float sc = ldexpf(1.0f, -l);
+                float a0 = 0.0f, e0 = 0.0f, a1 = 0.0f, e1 = 0.0f;
+#pragma unroll
+                for (int h = 0; h < QMAX; ++h)
+                    if (h < q) {
+                        ff_add(a0, e0, (float)fn[h], 0.0f);
+                        ff_add(a1, e1, (float)(dq_w(h)) * (float)fn[h], 0.0f);
+                    }
+                ff_add(fhi[0], flo[0], a0 * sc, e0 * sc);
+                ff_add(fhi[1], flo[1], a1 * sc, e1 * sc);
+            }
+        }
+        if (bad) atomicOr(&sm.status, (int)ST_NONFINITE);
+        if constexpr (sizeof(T) == 8) {
+            team_sum(macc);
+        } else {
+            team_sum_ff(fhi, flo, macc);
+            if (tid == 0) {
+                macc[0] *= d.b - d.a;
+                macc[1] *= (d.b - d.a) * d.lam;
+            }
+        }
+        if (tid == 0) {
+            // copy boundary: what leaves through x = a and x = b, sum over the
+            // populations of sigma 2^-Jmax-weighted telescoped stream terms
+            double flux[2] = {0.0, 0.0};
+            if (d.bc == 1) {
+                const double dxJ = sm.dx_l[d.Jmax];
+                for (int h = 1; h < q; ++h) {
+                    const int w = dq_w(h), a = w < 0 ? -w : w;
+                    const T *ph = Phi + (long long)h * (N + 1);
+                    double t = 0.0;
+                    for (int dl = 1; dl <= a; ++dl) {
+                        const long long eta = w > 0 ? -dl : dl - 1;
+                        t += (double)ph[at(eta)] - (double)ph[at(N + eta)];
+                    }
+                    t *= (w > 0 ? dxJ : -dxJ);
+                    flux[0] += t;
+                    flux[1] += (w * d.lam) * t;
+                }
+            }
+            for (int j = 0; j < 2; ++j) {
+                const double res = fabs(macc[j] - sm.mass[j] - flux[j]);
+                sm.audit = fmax(sm.audit, res);
+                sm.mass[j] = macc[j];
+            }
+            sm.steps += 1ULL;
+        }
+        sync();
+    }
+
     // sum of four products; FP32: compensated (Kahan) accumulation
     static __device__ __forceinline__ T dot4(T c0, T x0, T c1, T x1, T c2, T x2, T c3, T x3) {
         if constexpr (sizeof(T) == 8) {
@@ -1133,6 +1375,10 @@ struct Worker {
     // the FP32 path 2^-l (f+ + f-) is summed exactly per leaf into float-float
     // partials (relative error near 2^-44) and scaled by b - a at the end.
     __device__ void stream_and_audit() {
+        if constexpr (DQ) {
+            stream_dq();
+            return;
+        }
         const uint32_t *leaves = list(L_LEAF);
         double macc[3] = {0.0, 0.0, 0.0};
         float fhi[3] = {0.0f, 0.0f, 0.0f}, flo[3] = {0.0f, 0.0f, 0.0f};
@@ -1212,7 +1458,10 @@ struct Worker {
         for (long long k = tid; k < d.N; k += TS) {
             double mc[3], f[QMAX];
             for (int j = 0; j < nf; ++j) mc[j] = mcons[j * d.N + k];
-            equilibrium_populations<NF>(d, mc, f);
+            if constexpr (DQ)
+                dq_equilibrium_populations<q>(d, mc, f);
+            else
+                equilibrium_populations<NF>(d, mc, f);
             for (int h = 0; h < q; ++h) row(h, d.Jmax)[k] = (T)f[h];
         }
         if (tid == 0) sm.cur = M_R0;
@@ -1252,7 +1501,18 @@ struct Worker {
             int l = ent >> KBITS;
             long long k = ent & KMASK;
             double dx = sm.dx_l[l];
-            for (int j = 0; j < nf; ++j) macc[j] += dx * ((double)row(2 * j, l)[k] + (double)row(2 * j + 1, l)[k]);
+            if constexpr (DQ) {
+                double m0 = 0.0, m1 = 0.0;
+                for (int h = 0; h < q; ++h) {
+                    const double f = (double)row(h, l)[k];
+                    m0 += f;
+                    m1 += (dq_w(h) * d.lam) * f;
+                }
+                macc[0] += dx * m0;
+                macc[1] += dx * m1;
+            } else {
+                for (int j = 0; j < nf; ++j) macc[j] += dx * ((double)row(2 * j, l)[k] + (double)row(2 * j + 1, l)[k]);
+            }
         }
         team_sum(macc);
         if (tid == 0) {
@@ -1281,8 +1541,20 @@ struct Worker {
                                                     tab.pc[d.gamma]);
             sync();
         }
-        for (long long k = tid; k < d.N; k += TS)
-            for (int j = 0; j < nf; ++j) out[j * d.N + k] = (double)row(2 * j, d.Jmax)[k] + (double)row(2 * j + 1, d.Jmax)[k];
+        for (long long k = tid; k < d.N; k += TS) {
+            if constexpr (DQ) {
+                double m0 = 0.0, m1 = 0.0;
+                for (int h = 0; h < q; ++h) {
+                    const double f = (double)row(h, d.Jmax)[k];
+                    m0 += f;
+                    m1 += (dq_w(h) * d.lam) * f;
+                }
+                out[k] = m0;
+                out[d.N + k] = m1;
+            } else {
+                for (int j = 0; j < nf; ++j) out[j * d.N + k] = (double)row(2 * j, d.Jmax)[k] + (double)row(2 * j + 1, d.Jmax)[k];
+            }
+        }
         sync();
     }
 };
@@ -1391,11 +1663,23 @@ __device__ void run_team(TeamSmem<T> &sm, const Tables<T> &tab, BlockScratch &bx
         }
         __syncthreads();
     }
+    if constexpr (!WIDE) {
+        // D1Q3 / D1Q5 shallow water (gamma = 1 only)
+        if (sm.d.eq == 4) {
+            run_instance<T, 4, TS, false>(sm, tab, bx, a, tid, masks);
+            goto done;
+        }
+        if (sm.d.eq == 5) {
+            run_instance<T, 5, TS, false>(sm, tab, bx, a, tid, masks);
+            goto done;
+        }
+    }
     switch (sm.d.nf) {
     case 1: run_instance<T, 1, TS, WIDE>(sm, tab, bx, a, tid, masks); break;
     case 2: run_instance<T, 2, TS, WIDE>(sm, tab, bx, a, tid, masks); break;
     default: run_instance<T, 3, TS, WIDE>(sm, tab, bx, a, tid, masks); break;
     }
+done:
     if (local) {
         uint32_t *gr = sm.d.masks + (long long)sm.cur * W;
         const uint32_t *lr = smask + sm.cur * W;

@@ -34,7 +34,7 @@ unsigned char *g_scratch_dev[kMaxDevices] = {nullptr};
 
 size_t align256(size_t x) { return (x + 255) / 256 * 256; }
 
-int nfields(int eq) { return eq == MR_EQ_SW_VEC ? 2 : eq == MR_EQ_EULER_VEC ? 3 : (eq == 0 || eq == 1) ? 1 : 0; }
+int nfields(int eq) { return mrg_nfields(eq); }
 
 mr_status fail(mr_status code, const char *fmt, long long a = 0, long long b = 0) {
     char buf[256];
@@ -54,13 +54,15 @@ extern "C" mr_status mr_run_static(const mr_instance_desc *desc, int precision, 
     if (d.Jmin < 2 || d.Jmax < d.Jmin || d.Jmax > MAXLEV || d.gamma < 1 || d.gamma > 3 || nf == 0 || d.mu_bar < 0 ||
         (d.bc != MR_BC_PERIODIC && d.bc != MR_BC_COPY) || !(d.eps >= 0.0) || !(d.b > d.a) || !(d.lambda > 0.0))
         return fail(MR_ERR_ARG, "mr_run_static: invalid instance description");
-    for (int j = 0; j < nf; ++j)
+    for (int j = 0; j < mrg_nrates(d.eq); ++j)
         if (!(d.s[j] > 0.0 && d.s[j] <= 2.0)) return fail(MR_ERR_ARG, "mr_run_static: relaxation rate outside (0, 2]");
+    if ((d.eq == MR_EQ_SW_D1Q3 || d.eq == MR_EQ_SW_D1Q5) && d.gamma != 1)
+        return fail(MR_ERR_ARG, "mr_run_static: the D1Q3 / D1Q5 schemes are built with gamma = 1");
     const bool fp32 = precision == MR_FP32_MIXED;
     cudaStream_t s = (cudaStream_t)stream;
 
     // layout of the scratch area for this instance (same regions as a bound context)
-    const int q = 2 * nf;
+    const int q = mrg_npop(d.eq);
     const long long S = (1LL << (d.Jmax + 1)) - (1LL << d.Jmin), N = 1LL << d.Jmax;
     int W = 0;
     for (int l = d.Jmin; l <= d.Jmax; ++l) W += l >= 5 ? (1 << (l - 5)) : 1;
@@ -111,6 +113,7 @@ extern "C" mr_status mr_run_static(const mr_instance_desc *desc, int precision, 
     h.bc = d.bc;
     h.eq = d.eq;
     h.nf = nf;
+    if (d.eq == MR_EQ_SW_D1Q3 || d.eq == MR_EQ_SW_D1Q5) mrg_dq_inverse(d.eq, d.lambda, h.minv);
     h.mu_bar = d.mu_bar;
     h.gamma = d.gamma;
     h.Wtot = W;

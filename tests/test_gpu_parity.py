@@ -440,3 +440,92 @@ def test_wide_stencil_fp32_and_batch():
         assert_same_leaves(lvs, o, tol=1e-11)
         err = insts[i].dx * np.abs(s32.finest(i) - o.finest_moments()).sum(axis=1)
         assert np.all(err < 1e-4), (i, err)
+
+
+DQ_CASES = [
+    ("d1q3-copy-J9", lambda: W.random_smooth(9, W.EQ_SW_D1Q3, seed=100, eps=1e-4, bc=W.BC_COPY)),
+    ("d1q3-periodic-J10", lambda: W.random_smooth(10, W.EQ_SW_D1Q3, seed=101, eps=3e-4)),
+    ("d1q5-copy-J9", lambda: W.random_smooth(9, W.EQ_SW_D1Q5, seed=102, eps=1e-4, bc=W.BC_COPY)),
+    ("d1q5-periodic-J10", lambda: W.random_smooth(10, W.EQ_SW_D1Q5, seed=103, eps=3e-4)),
+    ("d1q5-jmin5", lambda: W.random_smooth(9, W.EQ_SW_D1Q5, seed=104, eps=1e-4, Jmin=5, bc=W.BC_COPY)),
+    ("dam-break-d1q3", lambda: W.shallow_water_dq("d1q3")),
+    ("dam-break-d1q5", lambda: W.shallow_water_dq("d1q5", s2=1.6)),
+]
+
+
+@pytest.mark.parametrize("name,make", DQ_CASES, ids=[c[0] for c in DQ_CASES])
+def test_d1q3_d1q5_lockstep_parity(name, make):
+    """Shallow water on one velocity set (Section 5.2): |v| = 2 lambda streams
+    two finest cells per side, sigma = 2 enlargement (D1Q5)."""
+    inst = make()
+    s = _solver(inst)
+    o = O.Oracle(params_of(inst))
+    for n in range(8):
+        R, vals, _ = gpu_state(s)
+        o.set_state(R, vals)
+        o.step()
+        s.advance(1)
+        R2, _, lvs = gpu_state(s)
+        assert np.array_equal(R2, o.get_state()[0]), f"step {n}: mesh differs"
+        assert_same_leaves(lvs, o)
+
+
+@pytest.mark.parametrize("name,make", DQ_CASES, ids=[c[0] for c in DQ_CASES])
+def test_d1q3_d1q5_free_running_parity(name, make):
+    inst = make()
+    s = _solver(inst)
+    o = oracle_of(inst)
+    for n in range(30):
+        o.step()
+        s.advance(1)
+    R, _, lvs = gpu_state(s)
+    assert np.array_equal(R, o.get_state()[0])
+    assert_same_leaves(lvs, o, tol=1e-11)
+    assert np.max(np.abs(s.finest() - o.finest_moments())) < 1e-11
+    m, res = s.audit()
+    assert np.allclose(m, o.mass(), rtol=1e-12, atol=1e-13)
+    assert res < 1e-12
+
+
+@pytest.mark.parametrize("eq,bc", [(W.EQ_SW_D1Q3, W.BC_PERIODIC), (W.EQ_SW_D1Q5, W.BC_COPY)])
+def test_d1q3_d1q5_arbitrary_graded_trees(eq, bc):
+    rng = np.random.default_rng(110 + eq + bc)
+    inst = W.random_smooth(10, eq, seed=111, bc=bc, eps=1e-4)
+    s = _solver(inst)
+    o = O.Oracle(params_of(inst))
+    R = random_graded_tree(inst.Jmin, inst.Jmax, rng, density=0.3, bc=bc)
+    base = O.equilibrium(params_of(inst), np.array([[1.2], [0.1]]))[:, :1]
+    vals = base + 0.02 * rng.normal(size=(inst.q, o.S))
+    s.set_state(0, R, vals)
+    o.set_state(R, vals)
+    o.lbm_step()
+    s.lbm_step()
+    _, _, lvs = gpu_state(s)
+    assert_same_leaves(lvs, o)
+    for n in range(4):
+        R, vals, _ = gpu_state(s)
+        o.set_state(R, vals)
+        o.step()
+        s.advance(1)
+        R2, _, lvs = gpu_state(s)
+        assert np.array_equal(R2, o.get_state()[0])
+        assert_same_leaves(lvs, o)
+
+
+def test_d1q3_d1q5_fp32_and_mixed_batch():
+    """A batch mixing every scheme (D1Q2^n, D1Q3, D1Q5) in one context, both
+    precisions: FP64 against the oracle, FP32 within 1e-4 in L1."""
+    insts = [W.random_smooth(8 + (j % 3), eq, seed=120 + j, eps=1e-4, bc=j % 2)
+             for j, eq in enumerate([W.EQ_SW_D1Q3, W.EQ_SW_D1Q5, W.EQ_EULER, W.EQ_BURGERS, W.EQ_SW_D1Q5,
+                                     W.EQ_SW, W.EQ_SW_D1Q3, W.EQ_ADVECTION])]
+    s64, s32 = _solver(insts), _solver(insts, precision=MR_FP32_MIXED)
+    s64.advance(12)
+    s32.advance(12)
+    for i in range(len(insts)):
+        o = oracle_of(insts[i])
+        o.step(12)
+        R, _, lvs = gpu_state(s64, i)
+        assert np.array_equal(R, o.get_state()[0]), i
+        assert_same_leaves(lvs, o, tol=1e-11)
+        err = insts[i].dx * np.abs(s32.finest(i) - o.finest_moments()).sum(axis=1)
+        assert np.all(err < 1e-4), (i, err)
