@@ -138,6 +138,9 @@ def make_workload(name: str, rank: int, n_batch: int = 4096):
     if name == "batch":
         insts = W.batch(n=n_batch, seed=12163 + rank)
         desc = f"batch of {n_batch} mixed D1Q2 advection/Burgers, D1Q2^2 shallow water, D1Q2^3 Euler; Jmax 8..14; eps 1e-5..1e-2"
+    elif name == "batch_sw":
+        insts = W.batch_sw(n=n_batch, seed=5202 + rank)
+        desc = f"batch of {n_batch} shallow water instances, D1Q3 / D1Q5 (Section 5.2); Jmax 8..14; eps 1e-5..1e-2"
     else:
         insts = [W.WORKLOADS[name]()]
         i = insts[0]
@@ -367,8 +370,8 @@ def main():
     ap.add_argument("--instances", type=int, default=4096, help="batch size (smaller only for profiling)")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="batch",
-                    choices=["batch", "advection", "burgers", "shallow", "sod", "test1", "test2", "test3", "test4",
-                             "sw_d1q3", "sw_d1q5"])
+                    choices=["batch", "batch_sw", "advection", "burgers", "shallow", "sod", "test1", "test2", "test3",
+                             "test4", "sw_d1q3", "sw_d1q5"])
     ap.add_argument("--block", type=int, default=None)
     ap.add_argument("--gamma", type=int, default=1, choices=[1, 2, 3],
                     help="prediction stencil half-width of every instance (Section 3.1)")

@@ -199,7 +199,9 @@ mr_status mr_autotune(mr_ctx *ctx, int nsteps, void *scratch, size_t scratch_byt
  * 4 weights of the first finest cell on the level-l window (k-2, k-1, k, k+1),
  * kind 1 the 4 weights on the window (2k-2, 2k-1, 2k, 2k+1) of level l+1 (used
  * next to a finer neighbour), kind 2 the 2 weights on (0, 1) for the leaf
- * k = 0 at a copy boundary.  The last finest cell uses the mirrored weights.
+ * k = 0 at a copy boundary; kinds 3, 4, 5 the same for the second finest cell
+ * from the edge (used by the populations with |v| = 2 lambda of D1Q5).  The
+ * last (second-to-last) finest cell uses the mirrored weights.
  * Host-only query, no device needed. */
 mr_status mr_reconstruction_coefficients(int dj, int kind, double *out);
 

@@ -862,7 +862,7 @@ mr_status mr_autotune(mr_ctx *c, int nsteps, void *scratch, size_t scratch_bytes
 }
 
 mr_status mr_reconstruction_coefficients(int dj, int kind, double *out) {
-    if (!out || dj < 0 || dj > MAXDJ || kind < 0 || kind > 2) return MR_ERR_ARG;
+    if (!out || dj < 0 || dj > MAXDJ || kind < 0 || kind > 5) return MR_ERR_ARG;
     static Tables<double> td;
     static Tables<float> tf;
     static bool made = false;
@@ -870,8 +870,9 @@ mr_status mr_reconstruction_coefficients(int dj, int kind, double *out) {
         make_tables(td, tf);
         made = true;
     }
-    const double *src = kind == 0 ? td.cf[dj] : kind == 1 ? td.t1[dj] : td.bf[dj];
-    int n = kind == 2 ? 2 : 4;
+    const double *src = kind == 0 ? td.cf[dj] : kind == 1 ? td.t1[dj] : kind == 2 ? td.bf[dj]
+                      : kind == 3 ? td.cf2[dj] : kind == 4 ? td.t12[dj] : td.bf2[dj];
+    int n = (kind == 2 || kind == 5) ? 2 : 4;
     for (int j = 0; j < n; ++j) out[j] = src[j];
     return MR_OK;
 }

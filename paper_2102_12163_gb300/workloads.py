@@ -196,6 +196,28 @@ def batch(n: int = 4096, seed: int = 12163, Jmin: int = 2, Jmax_range=(8, 14),
     return out
 
 
+def batch_sw(n: int = 4096, seed: int = 5202, Jmin: int = 2, Jmax_range=(8, 14),
+             eps_log10=(-5.0, -2.0)) -> list[Instance]:
+    """Batch of shallow water instances on one velocity set, half D1Q3 (lambda 2)
+    and half D1Q5 (lambda 3), periodic on [-1, 1], h piecewise constant in
+    [0.5, 2] with 1..6 jumps, u = 0, g = 1, relaxation s^2 in [1, 1.6]."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    out = []
+    for i in range(n):
+        eq = EQ_SW_D1Q3 if rng.random() < 0.5 else EQ_SW_D1Q5
+        J = int(rng.integers(Jmax_range[0], Jmax_range[1] + 1))
+        eps = float(10.0 ** rng.uniform(*eps_log10))
+        nj = int(rng.integers(1, 7))
+        jumps = np.sort(rng.uniform(-1.0, 1.0, nj))
+        s2 = float(rng.uniform(1.0, 1.6))
+        inst = Instance(f"w{i}", eq, Jmin, J, eps, 2.0 if eq == EQ_SW_D1Q3 else 3.0, -1.0, 1.0, BC_PERIODIC, 0.0,
+                        s=(s2,) if eq == EQ_SW_D1Q3 else (s2, 1.0, 1.0), eqp=1.0)
+        hh = avg_piecewise(cell_edges(-1.0, 1.0, J), jumps, rng.uniform(0.5, 2.0, nj + 1))
+        inst.m0 = np.stack([hh, np.zeros_like(hh)])
+        out.append(inst)
+    return out
+
+
 def random_smooth(Jmax: int, eq: int, seed: int, Jmin: int = 2, eps: float = 1e-3, bc: int = BC_PERIODIC,
                   nmodes: int = 3) -> Instance:
     """Small seeded instance with smooth plus step data, for parity tests."""

@@ -92,7 +92,7 @@ def test_batch_creation_checks_every_descriptor():
 def _table(dj, kind):
     out = (ctypes.c_double * 4)()
     assert capi.load().mr_reconstruction_coefficients(dj, kind, out) == capi.MR_OK
-    return np.array(out[: 2 if kind == 2 else 4])
+    return np.array(out[: 2 if kind in (2, 5) else 4])
 
 
 def _full_tree_to(Jmin, Jmax, lmax):
@@ -166,10 +166,51 @@ def test_tables_are_exact_dyadic_rationals():
     from fractions import Fraction
 
     for dj in range(0, 17):
-        for kind in (0, 1, 2):
-            if kind == 1 and dj == 0:
+        for kind in (0, 1, 2, 3, 4, 5):
+            if kind in (1, 4) and dj == 0:
                 continue
             t = _table(dj, kind)
             assert sum(Fraction(x) for x in t) == 1  # weights reproduce constants
             for x in t:
                 assert (Fraction(x) * 8 ** dj).denominator == 1
+
+
+@pytest.mark.parametrize("dj", [1, 2, 3, 6])
+def test_second_cell_tables_match_the_oracle(dj):
+    """Second finest cell from a leaf edge (streamed by the |v| = 2 lambda
+    populations of D1Q5): interior, finer-neighbour and copy-boundary weights
+    against the oracle's level-by-level prediction."""
+    Jmin, l = 2, 5
+    Jmax = l + dj
+    rng = np.random.default_rng(200 + dj)
+    cf2, t12, bf2 = _table(dj, 3), _table(dj, 4), _table(dj, 5)
+    R, off = _full_tree_to(Jmin, Jmax, l)
+    n = 1 << l
+    for bc in (O.BC_PERIODIC, O.BC_COPY):
+        p = O.Params(Jmin=Jmin, Jmax=Jmax, eq=O.EQ_BURGERS, lam=1.0, bc=bc)
+        o = O.Oracle(p)
+        vals = rng.normal(size=(2, o.S))
+        o.set_state(R, vals)
+        fin = o.finest()[0]
+        V = vals[0, off[l]:off[l + 1]]
+        for k in range(2, n - 2):
+            assert abs(fin[(k << dj) + 1] - cf2 @ V[[k - 2, k - 1, k, k + 1]]) < 1e-13
+            assert abs(fin[((k + 1) << dj) - 2] - cf2[::-1] @ V[[k - 1, k, k + 1, k + 2]]) < 1e-13
+        if bc == O.BC_COPY:
+            assert abs(fin[1] - bf2 @ V[[0, 1]]) < 1e-13
+            assert abs(fin[-2] - bf2 @ V[[n - 1, n - 2]]) < 1e-13
+    # finer left neighbour
+    p = O.Params(Jmin=Jmin, Jmax=Jmax, eq=O.EQ_BURGERS, lam=1.0, bc=O.BC_PERIODIC)
+    o = O.Oracle(p)
+    vals = rng.normal(size=(2, o.S))
+    k = 9
+    R2 = R.copy()
+    R2[off[l + 1] + 2 * (k - 1)] = R2[off[l + 1] + 2 * (k - 1) + 1] = 1
+    o.set_state(R2, vals)
+    fin = o.finest()[0]
+    V = vals[0, off[l]:off[l + 1]]
+    V1 = vals[0, off[l + 1]:off[l + 2]]
+    vkm1 = 0.5 * (V1[2 * k - 2] + V1[2 * k - 1])
+    tt = -0.125 * (V[k + 1] - vkm1)
+    w1 = np.array([V1[2 * k - 2], V1[2 * k - 1], V[k] + tt, V[k] - tt])
+    assert abs(fin[(k << dj) + 1] - t12 @ w1) < 1e-13
