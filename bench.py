@@ -156,7 +156,8 @@ def _oracle_task(args):
     import oracle as O
 
     p = O.Params(Jmin=inst.Jmin, Jmax=inst.Jmax, eq=inst.eq, lam=inst.lam, eps=inst.eps, gamma=inst.gamma,
-                 mu_bar=inst.mu_bar, bc=inst.bc, a=inst.a, b=inst.b, s=inst.s, eqp=inst.eqp)
+                 mu_bar=inst.mu_bar, bc=inst.bc, a=inst.a, b=inst.b, s=inst.s, eqp=inst.eqp,
+                    collision=inst.collision)
     o = O.Oracle(p)
     o.set_initial(inst.m0)
     o.step(warm)

@@ -26,6 +26,7 @@ _SRC = os.path.join(_HERE, "mrlbm_oracle.c")
 _LIB = os.path.join(_HERE, "liborc.so")
 
 BC_PERIODIC, BC_COPY = 0, 1
+COLLIDE_LEAVES, COLLIDE_RECONSTRUCTED = 0, 1
 EQ_ADVECTION, EQ_BURGERS, EQ_SW, EQ_EULER = 0, 1, 2, 3
 EQ_SW_D1Q3, EQ_SW_D1Q5 = 4, 5  # shallow water, one velocity set for h and hu (Section 5.2)
 NFIELDS = {EQ_ADVECTION: 1, EQ_BURGERS: 1, EQ_SW: 2, EQ_EULER: 3, EQ_SW_D1Q3: 2, EQ_SW_D1Q5: 2}
@@ -52,6 +53,7 @@ class _Params(ctypes.Structure):
         ("mu_bar", ctypes.c_int), ("bc", ctypes.c_int), ("eps", ctypes.c_double),
         ("a", ctypes.c_double), ("b", ctypes.c_double), ("eq", ctypes.c_int),
         ("lambda_", ctypes.c_double), ("s", ctypes.c_double * 3), ("eqp", ctypes.c_double),
+        ("collision", ctypes.c_int),
     ]
 
 
@@ -67,6 +69,7 @@ def lib():
         sp = P(_Params)
         sig = {
             "orc_nfields": (ctypes.c_int, [ctypes.c_int]),
+            "orc_collide": (None, [ctypes.c_void_p]),
             "orc_npop": (ctypes.c_int, [ctypes.c_int]),
             "orc_create": (ctypes.c_void_p, [sp]),
             "orc_free": (None, [ctypes.c_void_p]),
@@ -128,12 +131,14 @@ class Params:
     b: float = 1.0
     s: tuple = (1.0, 1.0, 1.0)
     eqp: float = 0.0
+    collision: int = 0  # 0 leaves collision, 1 reconstructed collision (Section 4.5)
     _c: _Params = field(default=None, repr=False, compare=False)
 
     def c(self) -> _Params:
         s = list(self.s) + [1.0] * (3 - len(self.s))
         return _Params(self.Jmin, self.Jmax, self.gamma, self.mu_bar, self.bc, self.eps,
-                       self.a, self.b, self.eq, self.lam, (ctypes.c_double * 3)(*s[:3]), self.eqp)
+                       self.a, self.b, self.eq, self.lam, (ctypes.c_double * 3)(*s[:3]), self.eqp,
+                       self.collision)
 
     @property
     def nf(self) -> int:
@@ -191,6 +196,10 @@ class Oracle:
     # scheme ----------------------------------------------------------
     def adapt(self) -> None:
         lib().orc_adapt(self._h)
+
+    def collide(self) -> None:
+        """The collision phase alone (leaves or reconstructed, per the parameters)."""
+        lib().orc_collide(self._h)
 
     def lbm_step(self) -> None:
         lib().orc_lbm_step(self._h)

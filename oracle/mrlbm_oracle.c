@@ -566,11 +566,79 @@ void orc_adapt(orc_state *st) {
 /* ------------------------------------------------------------------ */
 /* adaptive scheme L_A (Sections 4.3 and 4.5)                          */
 
+/* eq. reconstructedCollision on one leaf: the conserved moments stay, each
+ * relaxed moment becomes (1 - s) m + s times the mean over the leaf's 2^{Jmax-l}
+ * finest cells of its equilibrium evaluated on the reconstructed conserved
+ * moments there (fin: the reconstruction of every population on the finest
+ * level, row length nJ). */
+static void collide_reconstructed(const orc_params *p, double *f, long stride, const double *fin, long nJ,
+                                  long first, long ncell) {
+    int nf = orc_nfields(p->eq), q = orc_npop(p->eq);
+    double acc[ORC_MAXQ] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+    for (long i = first; i < first + ncell; ++i) {
+        double g[ORC_MAXQ], mc[ORC_MAXFIELDS], meq[ORC_MAXQ];
+        for (int h = 0; h < q; ++h) g[h] = fin[h * nJ + i];
+        orc_moments(p, g, mc, 1);
+        if (is_dq(p->eq)) {
+            double m[5] = {mc[0], mc[1], 0.0, 0.0, 0.0};
+            dq_equilibria(p, q, m, meq);
+            for (int r = 2; r < q; ++r) acc[r] = acc[r] + meq[r];
+        } else {
+            equilibria(p, mc, meq);
+            for (int r = 0; r < nf; ++r) acc[r] = acc[r] + meq[r];
+        }
+    }
+    double inv = 1.0 / (double)ncell;
+    if (is_dq(p->eq)) {
+        double M[5][5], Mi[5][5], m[5];
+        dq_matrices(p, q, M, Mi);
+        for (int i = 0; i < q; ++i) {
+            double a = 0.0;
+            for (int h = 0; h < q; ++h) a = a + M[i][h] * f[h * stride];
+            m[i] = a;
+        }
+        for (int i = 2; i < q; ++i) m[i] = (1.0 - p->s[i - 2]) * m[i] + p->s[i - 2] * (acc[i] * inv);
+        for (int h = 0; h < q; ++h) {
+            double a = 0.0;
+            for (int i = 0; i < q; ++i) a = a + Mi[h][i] * m[i];
+            f[h * stride] = a;
+        }
+        return;
+    }
+    for (int i = 0; i < nf; ++i) {
+        double fp = f[(2 * i) * stride], fm = f[(2 * i + 1) * stride];
+        double mc = fp + fm, mn = p->lambda * (fp - fm);
+        double mstar = (1.0 - p->s[i]) * mn + p->s[i] * (acc[i] * inv);
+        double g = mstar / p->lambda;
+        f[(2 * i) * stride] = 0.5 * (mc + g);
+        f[(2 * i + 1) * stride] = 0.5 * (mc - g);
+    }
+}
+
 static void collide_leaves(orc_state *st) {
+    if (st->p.collision == ORC_COLLIDE_RECONSTRUCTED) {
+        /* reconstruction of the pre-collision populations on every finest cell */
+        long nJ = ncells(st->p.Jmax);
+        memcpy(st->tmp, st->V, sizeof(double) * st->S * st->q);
+        fill_values(st, st->tmp);
+        double *fin = (double *)malloc(sizeof(double) * nJ * st->q);
+        for (int h = 0; h < st->q; ++h)
+            for (long i = 0; i < nJ; ++i) fin[h * nJ + i] = VAL(st, st->tmp, h, st->p.Jmax, i);
+        for (int l = st->p.Jmin; l <= st->p.Jmax; ++l) {
+            int dj = st->p.Jmax - l;
+            for (long k = 0; k < ncells(l); ++k)
+                if (is_leaf(st, l, k))
+                    collide_reconstructed(&st->p, &VAL(st, st->V, 0, l, k), st->S, fin, nJ, k << dj, 1L << dj);
+        }
+        free(fin);
+        return;
+    }
     for (int l = st->p.Jmin; l <= st->p.Jmax; ++l)
         for (long k = 0; k < ncells(l); ++k)
             if (is_leaf(st, l, k)) collide_cell(&st->p, &VAL(st, st->V, 0, l, k), st->S);
 }
+
+void orc_collide(orc_state *st) { collide_leaves(st); }
 
 void orc_lbm_step(orc_state *st) {
     const orc_params *p = &st->p;

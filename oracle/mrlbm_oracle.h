@@ -50,7 +50,14 @@ typedef struct {
     double s[ORC_MAXFIELDS];   /* relaxation rate of the non-conserved moment of each field
                                   (D1Q3 / D1Q5: of the moments m^2, m^3, m^4) */
     double eqp;     /* advection velocity c | unused | gravity g | gas constant gamma_g */
+    int collision;  /* ORC_COLLIDE_LEAVES or ORC_COLLIDE_RECONSTRUCTED */
 } orc_params;
+
+/* collision of the adaptive scheme (Section 4.5): on the leaf averages
+ * (eq. LeavesCollision) or with the equilibria averaged over the leaf's
+ * reconstructed finest cells (eq. reconstructedCollision) */
+#define ORC_COLLIDE_LEAVES 0
+#define ORC_COLLIDE_RECONSTRUCTED 1
 
 typedef struct orc_state orc_state;
 
@@ -81,6 +88,8 @@ void orc_get_state(const orc_state *st, unsigned char *R, double *values);
 void orc_adapt(orc_state *st);
 /* One application of the adaptive scheme on the current mesh: leaves
  * collision (eq. LeavesCollision) and compact stream (eq. AdaptiveStreamPhase). */
+/* the collision phase alone (S1 of the adaptive scheme), for tests */
+void orc_collide(orc_state *st);
 void orc_lbm_step(orc_state *st);
 /* orc_adapt followed by orc_lbm_step. */
 void orc_step(orc_state *st);

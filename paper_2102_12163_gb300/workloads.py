@@ -34,6 +34,7 @@ import numpy as np
 
 EQ_ADVECTION, EQ_BURGERS, EQ_SW, EQ_EULER = 0, 1, 2, 3
 EQ_SW_D1Q3, EQ_SW_D1Q5 = 4, 5  # shallow water on one velocity set (Section 5.2)
+COLLIDE_LEAVES, COLLIDE_RECONSTRUCTED = 0, 1
 NFIELDS = {EQ_ADVECTION: 1, EQ_BURGERS: 1, EQ_SW: 2, EQ_EULER: 3, EQ_SW_D1Q3: 2, EQ_SW_D1Q5: 2}
 NPOP = {EQ_ADVECTION: 2, EQ_BURGERS: 2, EQ_SW: 4, EQ_EULER: 6, EQ_SW_D1Q3: 3, EQ_SW_D1Q5: 5}
 BC_PERIODIC, BC_COPY = 0, 1
@@ -58,6 +59,7 @@ class Instance:
     mu_bar: int = 0
     s: tuple = (1.0, 1.0, 1.0)
     eqp: float = 0.0  # advection velocity | unused | gravity | gas constant | gravity (D1Q3, D1Q5)
+    collision: int = 0  # 0: leaves collision, 1: reconstructed collision (Section 4.5)
     m0: np.ndarray = field(default=None, repr=False)  # (nf, 2^Jmax) cell averages
 
     @property

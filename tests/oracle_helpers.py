@@ -9,7 +9,8 @@ from paper_2102_12163_gb300 import workloads as W
 
 def params_of(inst: W.Instance) -> O.Params:
     return O.Params(Jmin=inst.Jmin, Jmax=inst.Jmax, eq=inst.eq, lam=inst.lam, eps=inst.eps, gamma=inst.gamma,
-                    mu_bar=inst.mu_bar, bc=inst.bc, a=inst.a, b=inst.b, s=inst.s, eqp=inst.eqp)
+                    mu_bar=inst.mu_bar, bc=inst.bc, a=inst.a, b=inst.b, s=inst.s, eqp=inst.eqp,
+                    collision=inst.collision)
 
 
 def oracle_of(inst: W.Instance) -> O.Oracle:
