@@ -376,6 +376,8 @@ def main():
     ap.add_argument("--block", type=int, default=None)
     ap.add_argument("--gamma", type=int, default=1, choices=[1, 2, 3],
                     help="prediction stencil half-width of every instance (Section 3.1)")
+    ap.add_argument("--collision", default="leaves", choices=["leaves", "reconstructed"],
+                    help="collision of the adaptive scheme (Section 4.5)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true", help="same as --precision fp32")
     ap.add_argument("--precision", default="both", choices=["both", "fp32", "fp64"],
@@ -387,12 +389,14 @@ def main():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     insts, desc = make_workload(args.workload, rank, args.instances)
-    if args.gamma != 1:
+    if args.gamma != 1 or args.collision != "leaves":
+        coll = 1 if args.collision == "reconstructed" else 0
         for i in range(len(insts)):
-            m0 = insts[i].m0
-            insts[i] = insts[i].with_(gamma=args.gamma)
-            insts[i].m0 = m0
-        desc += f"; prediction stencil gamma = {args.gamma}"
+            insts[i] = insts[i].with_(gamma=args.gamma, collision=coll)
+        if args.gamma != 1:
+            desc += f"; prediction stencil gamma = {args.gamma}"
+        if coll:
+            desc += "; reconstructed collision"
     hbm, hbm_src = peaks()
 
     if args.impl == "reference":

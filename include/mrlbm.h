@@ -86,7 +86,15 @@ typedef struct {
     double lambda;    /* lattice velocity, dt = dx_Jmax / lambda */
     double s[3];      /* relaxation rate of the non-conserved moment of each field */
     double eq_param;  /* see mr_equilibrium */
+    int collision;    /* mr_collision */
 } mr_instance_desc;
+
+/* Collision of the adaptive scheme (Section 4.5): on the leaf values (eq.
+ * LeavesCollision, the default), or with the equilibria of the relaxed moments
+ * averaged over the leaf's 2^(Jmax-l) reconstructed finest cells (eq.
+ * reconstructedCollision; costs a reconstruction of the whole finest level
+ * per step). */
+typedef enum { MR_COLLIDE_LEAVES = 0, MR_COLLIDE_RECONSTRUCTED = 1 } mr_collision;
 
 /* ---- creation -------------------------------------------------------- */
 
@@ -100,6 +108,9 @@ mr_status mr_mesh_init(mr_ctx **out, int Jmin, int Jmax, int gamma, double eps, 
  * non-conserved moments, equilibrium eq with parameter *eq_params. */
 mr_status lbm_scheme(mr_ctx *ctx, int d, int q, double lambda, const double *s, int eq,
                      const double *eq_params);
+
+/* Collision kind (mr_collision) of every instance of the context; before mr_bind. */
+mr_status mr_set_collision(mr_ctx *ctx, int kind);
 
 /* n independent instances in one context (batched persistent launch). */
 mr_status mr_batch_create(mr_ctx **out, const mr_instance_desc *desc, int n, int precision);

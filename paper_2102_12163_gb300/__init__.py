@@ -30,6 +30,7 @@ def _desc(inst: "workloads.Instance") -> capi.mr_instance_desc:
     for j in range(3):
         d.s[j] = s[j]
     d.eq_param = inst.eqp
+    d.collision = inst.collision
     return d
 
 
@@ -57,6 +58,8 @@ class MRLBM:
             s = (ctypes.c_double * 3)(*(list(inst.s) + [1.0] * 3)[:3])
             eqp = ctypes.c_double(inst.eqp)
             capi.check(self.h, self.lib.lbm_scheme(self.h, 1, inst.q, inst.lam, s, _EQ[inst.eq], ctypes.byref(eqp)))
+            if inst.collision:
+                capi.check(self.h, self.lib.mr_set_collision(self.h, inst.collision))
         else:
             arr = (capi.mr_instance_desc * len(self.instances))(*[_desc(i) for i in self.instances])
             capi.check(None, self.lib.mr_batch_create(ctypes.byref(h), arr, len(self.instances), precision))

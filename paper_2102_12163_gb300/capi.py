@@ -15,6 +15,7 @@ MR_FP64, MR_FP32_MIXED = 0, 1
 MR_BC_PERIODIC, MR_BC_COPY = 0, 1
 MR_EQ_ADVECTION, MR_EQ_BURGERS, MR_EQ_SW_VEC, MR_EQ_EULER_VEC = 0, 1, 2, 3
 MR_EQ_SW_D1Q3, MR_EQ_SW_D1Q5 = 4, 5
+MR_COLLIDE_LEAVES, MR_COLLIDE_RECONSTRUCTED = 0, 1
 
 STATUS_NAMES = {0: "MR_OK", -1: "MR_ERR_ARG", -2: "MR_ERR_CUDA", -3: "MR_ERR_CAPACITY",
                 -4: "MR_ERR_NONFINITE", -5: "MR_ERR_TIMEOUT", -6: "MR_ERR_STATE"}
@@ -25,7 +26,7 @@ class mr_instance_desc(ctypes.Structure):
         ("Jmin", ctypes.c_int), ("Jmax", ctypes.c_int), ("gamma", ctypes.c_int), ("mu_bar", ctypes.c_int),
         ("bc", ctypes.c_int), ("eq", ctypes.c_int), ("eps", ctypes.c_double), ("a", ctypes.c_double),
         ("b", ctypes.c_double), ("lambda_", ctypes.c_double), ("s", ctypes.c_double * 3),
-        ("eq_param", ctypes.c_double),
+        ("eq_param", ctypes.c_double), ("collision", ctypes.c_int),
     ]
 
 
@@ -53,6 +54,7 @@ SIGNATURES = {
     "mr_stats": [_vp, _P(ctypes.c_ulonglong), _P(ctypes.c_ulonglong), _P(ctypes.c_longlong)],
     "mr_set_launch": [_vp, _i, _i],
     "mr_set_order": [_vp, _i],
+    "mr_set_collision": [_vp, _i],
     "mr_autotune": [_vp, _i, _vp, ctypes.c_size_t, _P(_i), _P(_i), _P(ctypes.c_float)],
     "mr_reconstruction_coefficients": [_i, _i, _P(_d)],
     "mr_phase_times": [_vp, _i, _P(ctypes.c_ulonglong), _i],

@@ -72,6 +72,8 @@ void dq_inverse(int eq, double lambda, double inv[5][5]) {
 }
 
 int nwords_h(int l) { return l >= 5 ? (1 << (l - 5)) : 1; }
+// instances that need the general kernel variant
+bool general_of(const InstDesc &h) { return h.gamma > 1 || h.collision != 0; }
 // compiled scheme variant of the kernels: D1Q2^n by field count, D1Q3, D1Q5
 int variant_of(int eq) { return eq == MR_EQ_SW_D1Q3 ? 4 : eq == MR_EQ_SW_D1Q5 ? 5 : nfields_of(eq); }
 
@@ -130,6 +132,8 @@ static int check_desc(mr_ctx *c, const mr_instance_desc &d, int i) {
         return c->fail(MR_ERR_ARG, "instance %d: need 2 <= Jmin <= Jmax <= %d (got %d, %d)", i, MAXLEV, d.Jmin, d.Jmax);
     if (d.gamma < 1 || d.gamma > 3) return c->fail(MR_ERR_ARG, "instance %d: gamma must be 1, 2 or 3", i);
     if (d.mu_bar < 0 || d.mu_bar > 30) return c->fail(MR_ERR_ARG, "instance %d: mu_bar out of range", i);
+    if (d.collision != MR_COLLIDE_LEAVES && d.collision != MR_COLLIDE_RECONSTRUCTED)
+        return c->fail(MR_ERR_ARG, "instance %d: collision must be 0 (leaves) or 1 (reconstructed)", i);
     if (d.bc != MR_BC_PERIODIC && d.bc != MR_BC_COPY) return c->fail(MR_ERR_ARG, "instance %d: bad boundary", i);
     if (nfields_of(d.eq) == 0) return c->fail(MR_ERR_ARG, "instance %d: bad equilibrium", i);
     if (!(d.eps >= 0.0) || !(d.b > d.a) || !(d.lambda > 0.0))
@@ -182,6 +186,7 @@ static void layout(mr_ctx *c) {
         if (d.eq == MR_EQ_SW_D1Q3 || d.eq == MR_EQ_SW_D1Q5) dq_inverse(d.eq, d.lambda, h.minv);
         h.mu_bar = d.mu_bar;
         h.gamma = d.gamma;
+        h.collision = d.collision;
         h.Wtot = W;
         h.eps = d.eps;
         h.a = d.a;
@@ -304,13 +309,14 @@ static int launch_group(mr_ctx *c, int phases, int nsteps, const int *order, int
     return MR_OK;
 }
 
-// A launch over the instances: the queue order puts the gamma = 1 instances
-// first; each group runs in the kernel variant compiled for its stencils.
+// A launch over the instances: the queue order puts the instances of the fast
+// kernel variant (gamma = 1, leaves collision) first; the others run in the
+// general variant (wide stencils, reconstructed collision).
 static int launch(mr_ctx *c, int phases, int nsteps, int only_inst, const void *aux0, const void *aux1) {
     if (!c->bound) return c->fail(MR_ERR_STATE, "context not bound to a workspace");
     if (only_inst >= 0)
         return launch_group(c, phases, nsteps, (const int *)(c->ws + c->off_ident) + only_inst, 1,
-                            c->hdesc[only_inst].gamma > 1, aux0, aux1);
+                            general_of(c->hdesc[only_inst]), aux0, aux1);
     const int *order = (const int *)(c->ws + c->off_order);
     int rc = MR_OK;
     if (c->n_narrow > 0) rc = launch_group(c, phases, nsteps, order, c->n_narrow, false, aux0, aux1);
@@ -458,7 +464,7 @@ static int upload_order(mr_ctx *c) {
     std::vector<int> order(n);
     for (int i = 0; i < n; ++i) order[i] = i;
     std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
-        if ((dd[x].gamma > 1) != (dd[y].gamma > 1)) return dd[x].gamma == 1;  // kernel variant groups
+        if (general_of(dd[x]) != general_of(dd[y])) return !general_of(dd[x]);  // kernel variant groups
         const int vx = variant_of(dd[x].eq), vy = variant_of(dd[y].eq);
         if (c->order_by_fields && vx != vy) return vx > vy;
         double cx = (double)npop_of(dd[x].eq) * std::ldexp(1.0, dd[x].Jmax);
@@ -467,7 +473,7 @@ static int upload_order(mr_ctx *c) {
     });
     c->order_host = order;
     c->n_narrow = 0;
-    for (int i = 0; i < n; ++i) c->n_narrow += dd[i].gamma == 1;
+    for (int i = 0; i < n; ++i) c->n_narrow += !general_of(dd[i]);
     return c->cuda(cudaMemcpyAsync(c->ws + c->off_order, c->order_host.data(), sizeof(int) * n, cudaMemcpyHostToDevice,
                                    c->stream),
                    "upload");
@@ -791,6 +797,13 @@ mr_status mr_set_launch(mr_ctx *c, int block, int grid) {
     c->block = block;
     c->grid_req = grid;
     if (c->bound) return (mr_status)configure(c);
+    return MR_OK;
+}
+
+mr_status mr_set_collision(mr_ctx *c, int kind) {
+    if (!c || (kind != MR_COLLIDE_LEAVES && kind != MR_COLLIDE_RECONSTRUCTED)) return MR_ERR_ARG;
+    if (c->bound) return (mr_status)c->fail(MR_ERR_STATE, "mr_set_collision after mr_bind");
+    for (auto &d : c->desc) d.collision = kind;
     return MR_OK;
 }
 

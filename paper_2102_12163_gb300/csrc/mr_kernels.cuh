@@ -593,6 +593,135 @@ struct Worker {
         }
     }
 
+    // equilibria of the relaxed moments at one cell (populations g)
+    __device__ __forceinline__ void relaxed_equilibria(const T *g, T *meq) const {
+        if constexpr (DQ) {
+            const T lam = (T)d.lam;
+            T h = T(0), hu = T(0);
+#pragma unroll
+            for (int c = 0; c < q; ++c) {
+                h = h + g[c];
+                hu = hu + ((T)dq_w(c) * lam) * g[c];
+            }
+            meq[0] = (hu * hu) / h + (T(0.5) * (T)d.eqp) * (h * h);
+            if constexpr (q == 5) {
+                meq[1] = (lam * lam) * hu;
+                meq[2] = (lam * lam) * meq[0];
+            }
+        } else {
+            using A = Ar<T>;
+            T mc[NF];
+#pragma unroll
+            for (int i = 0; i < NF; ++i) mc[i] = A::add(g[2 * i], g[2 * i + 1]);
+            equilibria<T, NF>(d.eq, (T)d.eqp, mc, meq);
+        }
+    }
+
+    // S1 with the reconstructed collision (Section 4.5, eq. reconstructedCollision):
+    // the pre-collision populations are reconstructed on every finest cell
+    // (projection up the tree, prediction of every other cell level by level);
+    // each warp averages, one leaf at a time, the equilibria of the relaxed
+    // moments over the leaf's 2^dj finest cells (into the interface array, free
+    // until S4); then every leaf relaxes towards those averages.
+    __device__ __noinline__ void collide_reconstructed() {
+        upsweep();
+        sync();
+        const uint32_t *R = mask(sm.cur);
+        for (int l = d.Jmin + 1; l <= d.Jmax; ++l) {
+            const long long n = 1LL << l;
+            const uint32_t *rl = R + sm.woff[l];
+            for (long long k = tid; k < n; k += TS)
+                if (!((rl[k >> 5] >> (k & 31)) & 1u))
+                    for (int h = 0; h < q; ++h)
+                        row(h, l)[k] = predict_g<T>(row(h, l - 1), k >> 1, (int)(k & 1), l - 1, d.bc, d.gamma,
+                                                    tab.pc[d.gamma]);
+            sync();
+        }
+        constexpr int NR = DQ ? q - 2 : nf;  // relaxed moments
+        constexpr int NWARP = TS / 32;
+        const int lane = tid & 31, warp = tid >> 5;
+        const uint32_t *leaves = list(L_LEAF);
+        const long long stride = d.N + 1;
+        for (int i = warp; i < sm.nleaf; i += NWARP) {
+            const uint32_t ent = leaves[i];
+            const int l = ent >> KBITS;
+            const long long k = ent & KMASK;
+            const int dj = d.Jmax - l;
+            const long long first = k << dj, ncell = 1LL << dj;
+            T acc[3] = {T(0), T(0), T(0)};
+            for (long long c = first + lane; c < first + ncell; c += 32) {
+                T g[QMAX], meq[3];
+#pragma unroll
+                for (int h = 0; h < QMAX; ++h)
+                    if (h < q) g[h] = row(h, d.Jmax)[c];
+                relaxed_equilibria(g, meq);
+#pragma unroll
+                for (int r = 0; r < NR; ++r) acc[r] = acc[r] + meq[r];
+            }
+#pragma unroll
+            for (int r = 0; r < NR; ++r)
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) acc[r] = acc[r] + __shfl_xor_sync(FULL, acc[r], o);
+            if (lane == 0)
+#pragma unroll
+                for (int r = 0; r < NR; ++r) Phi[r * stride + i] = acc[r] * (T)ldexpf(1.0f, -dj);
+        }
+        sync();
+        for (int i = tid; i < sm.nleaf; i += TS) {
+            const uint32_t ent = leaves[i];
+            const int l = ent >> KBITS;
+            const long long k = ent & KMASK;
+            T f[QMAX], mavg[3];
+#pragma unroll
+            for (int h = 0; h < QMAX; ++h)
+                if (h < q) f[h] = row(h, l)[k];
+#pragma unroll
+            for (int r = 0; r < NR; ++r) mavg[r] = Phi[r * stride + i];
+            if constexpr (DQ) {
+                const T lam = (T)d.lam;
+                T m[q];
+#pragma unroll
+                for (int r = 0; r < q; ++r) m[r] = T(0);
+#pragma unroll
+                for (int h = 0; h < q; ++h) {
+                    const T v = (T)dq_w(h) * lam;
+                    T x = f[h];
+#pragma unroll
+                    for (int r = 0; r < q; ++r) {
+                        m[r] = m[r] + x;
+                        x = x * v;
+                    }
+                }
+                T dm[q];
+#pragma unroll
+                for (int r = 2; r < q; ++r) dm[r] = (T)d.s[r - 2] * (mavg[r - 2] - m[r]);
+#pragma unroll
+                for (int h = 0; h < q; ++h) {
+                    T a = T(0);
+#pragma unroll
+                    for (int r = 2; r < q; ++r) a = a + (T)d.minv[h][r] * dm[r];
+                    f[h] = f[h] + a;
+                }
+            } else {
+                using A = Ar<T>;
+                const T lam = (T)d.lam;
+#pragma unroll
+                for (int j = 0; j < NF; ++j) {
+                    const T mc = A::add(f[2 * j], f[2 * j + 1]), mn = A::mul(lam, A::sub(f[2 * j], f[2 * j + 1]));
+                    const T sj = (T)d.s[j];
+                    const T mstar = A::add(A::mul(A::sub(T(1), sj), mn), A::mul(sj, mavg[j]));
+                    const T g = A::div(mstar, lam);
+                    f[2 * j] = A::mul(T(0.5), A::add(mc, g));
+                    f[2 * j + 1] = A::mul(T(0.5), A::sub(mc, g));
+                }
+            }
+#pragma unroll
+            for (int h = 0; h < QMAX; ++h)
+                if (h < q) row(h, l)[k] = f[h];
+        }
+        sync();
+    }
+
     // ---- A1 / S2: projection sweep, fine to coarse ---------------------------
     __device__ void upsweep() {
         const uint32_t *li = list(L_INT);
@@ -1047,7 +1176,14 @@ struct Worker {
     // ---- one step of the adaptive scheme on the current mesh -----------------
     __device__ void lbm_step() {
         tick(NPHASE);
-        collide_all();          // S1
+        if constexpr (WIDE) {
+            if (d.collision)
+                collide_reconstructed();  // S1, eq. reconstructedCollision
+            else
+                collide_all();
+        } else {
+            collide_all();      // S1
+        }
         sync();
         tick(T_COLLIDE);
         upsweep();              // S2
@@ -1063,12 +1199,12 @@ struct Worker {
 
     // S4: first / last finest-cell values of every leaf -> Phi
     __device__ void reconstruct_edges() {
-        if constexpr (WIDE) {
-            reconstruct_wide();
+        if constexpr (DQ) {
+            reconstruct_dq();  // gamma = 1 (the tables)
             return;
         }
-        if constexpr (DQ) {
-            reconstruct_dq();
+        if constexpr (WIDE) {
+            reconstruct_wide();
             return;
         }
         const uint32_t *R = mask(sm.cur);
@@ -1164,11 +1300,13 @@ struct Worker {
                     rfirst = rlast = row(h, l)[k];
                 } else {
                     if (need_first)
-                        rfirst = g == 2 ? edge_walk<T, 2, false>(rb, d.Jmin, d.Jmax, d.bc, R, sm.woff, c, l, k)
-                                        : edge_walk<T, 3, false>(rb, d.Jmin, d.Jmax, d.bc, R, sm.woff, c, l, k);
+                        rfirst = g == 1   ? edge_walk<T, 1, false>(rb, d.Jmin, d.Jmax, d.bc, R, sm.woff, c, l, k)
+                                 : g == 2 ? edge_walk<T, 2, false>(rb, d.Jmin, d.Jmax, d.bc, R, sm.woff, c, l, k)
+                                          : edge_walk<T, 3, false>(rb, d.Jmin, d.Jmax, d.bc, R, sm.woff, c, l, k);
                     if (need_last)
-                        rlast = g == 2 ? edge_walk<T, 2, true>(rb, d.Jmin, d.Jmax, d.bc, R, sm.woff, c, l, k)
-                                       : edge_walk<T, 3, true>(rb, d.Jmin, d.Jmax, d.bc, R, sm.woff, c, l, k);
+                        rlast = g == 1   ? edge_walk<T, 1, true>(rb, d.Jmin, d.Jmax, d.bc, R, sm.woff, c, l, k)
+                                : g == 2 ? edge_walk<T, 2, true>(rb, d.Jmin, d.Jmax, d.bc, R, sm.woff, c, l, k)
+                                         : edge_walk<T, 3, true>(rb, d.Jmin, d.Jmax, d.bc, R, sm.woff, c, l, k);
                 }
                 T *ph = Phi + (long long)h * (d.N + 1);
                 if (plus) {
@@ -1663,23 +1801,15 @@ __device__ void run_team(TeamSmem<T> &sm, const Tables<T> &tab, BlockScratch &bx
         }
         __syncthreads();
     }
-    if constexpr (!WIDE) {
-        // D1Q3 / D1Q5 shallow water (gamma = 1 only)
-        if (sm.d.eq == 4) {
-            run_instance<T, 4, TS, false>(sm, tab, bx, a, tid, masks);
-            goto done;
-        }
-        if (sm.d.eq == 5) {
-            run_instance<T, 5, TS, false>(sm, tab, bx, a, tid, masks);
-            goto done;
-        }
-    }
-    switch (sm.d.nf) {
+    // scheme variant: D1Q2^nf, or D1Q3 / D1Q5 shallow water (equilibria 4, 5)
+    const int var = sm.d.eq == 4 ? 4 : sm.d.eq == 5 ? 5 : sm.d.nf;
+    switch (var) {
     case 1: run_instance<T, 1, TS, WIDE>(sm, tab, bx, a, tid, masks); break;
     case 2: run_instance<T, 2, TS, WIDE>(sm, tab, bx, a, tid, masks); break;
+    case 4: run_instance<T, 4, TS, WIDE>(sm, tab, bx, a, tid, masks); break;
+    case 5: run_instance<T, 5, TS, WIDE>(sm, tab, bx, a, tid, masks); break;
     default: run_instance<T, 3, TS, WIDE>(sm, tab, bx, a, tid, masks); break;
     }
-done:
     if (local) {
         uint32_t *gr = sm.d.masks + (long long)sm.cur * W;
         const uint32_t *lr = smask + sm.cur * W;

@@ -56,6 +56,8 @@ extern "C" mr_status mr_run_static(const mr_instance_desc *desc, int precision, 
         return fail(MR_ERR_ARG, "mr_run_static: invalid instance description");
     for (int j = 0; j < mrg_nrates(d.eq); ++j)
         if (!(d.s[j] > 0.0 && d.s[j] <= 2.0)) return fail(MR_ERR_ARG, "mr_run_static: relaxation rate outside (0, 2]");
+    if (d.collision != MR_COLLIDE_LEAVES && d.collision != MR_COLLIDE_RECONSTRUCTED)
+        return fail(MR_ERR_ARG, "mr_run_static: collision must be 0 or 1");
     if ((d.eq == MR_EQ_SW_D1Q3 || d.eq == MR_EQ_SW_D1Q5) && d.gamma != 1)
         return fail(MR_ERR_ARG, "mr_run_static: the D1Q3 / D1Q5 schemes are built with gamma = 1");
     const bool fp32 = precision == MR_FP32_MIXED;
@@ -116,6 +118,7 @@ extern "C" mr_status mr_run_static(const mr_instance_desc *desc, int precision, 
     if (d.eq == MR_EQ_SW_D1Q3 || d.eq == MR_EQ_SW_D1Q5) mrg_dq_inverse(d.eq, d.lambda, h.minv);
     h.mu_bar = d.mu_bar;
     h.gamma = d.gamma;
+    h.collision = d.collision;
     h.Wtot = W;
     h.eps = d.eps;
     h.a = d.a;
@@ -163,7 +166,7 @@ extern "C" mr_status mr_run_static(const mr_instance_desc *desc, int precision, 
     a.queue = (int *)(base + oQueue);
     a.tables = base + oTab + (fp32 ? sizeof(Tables<double>) : 0);
     a.smem_mask_words = W <= fit ? W : 0;
-    a.wide = d.gamma > 1 ? 1 : 0;
+    a.wide = (d.gamma > 1 || d.collision != 0) ? 1 : 0;
     const int phases[3] = {PH_INIT_FULL, PH_ADAPT | PH_STEP, PH_FINEST};
     const int steps[3] = {0, nsteps, 0};
     for (int i = 0; i < 3; ++i) {

@@ -529,3 +529,67 @@ def test_d1q3_d1q5_fp32_and_mixed_batch():
         assert_same_leaves(lvs, o, tol=1e-11)
         err = insts[i].dx * np.abs(s32.finest(i) - o.finest_moments()).sum(axis=1)
         assert np.all(err < 1e-4), (i, err)
+
+
+RC = W.COLLIDE_RECONSTRUCTED
+RECOLL_CASES = [
+    ("rc-burgers-copy", lambda: W.random_smooth(10, W.EQ_BURGERS, seed=130, eps=1e-4, bc=W.BC_COPY).with_(collision=RC)),
+    ("rc-euler-periodic", lambda: W.random_smooth(10, W.EQ_EULER, seed=131, eps=3e-4).with_(collision=RC)),
+    ("rc-sw-copy", lambda: W.random_smooth(9, W.EQ_SW, seed=132, eps=1e-4, bc=W.BC_COPY).with_(collision=RC)),
+    ("rc-d1q5-periodic", lambda: W.random_smooth(9, W.EQ_SW_D1Q5, seed=133, eps=1e-4).with_(collision=RC)),
+    ("rc-d1q3-copy", lambda: W.random_smooth(9, W.EQ_SW_D1Q3, seed=134, eps=1e-4, bc=W.BC_COPY).with_(collision=RC)),
+    ("rc-g2-euler", lambda: W.random_smooth(9, W.EQ_EULER, seed=135, eps=1e-4).with_(collision=RC, gamma=2)),
+    ("rc-testIV", lambda: W.scalar_test("IV").with_(collision=RC)),
+]
+
+
+@pytest.mark.parametrize("name,make", RECOLL_CASES, ids=[c[0] for c in RECOLL_CASES])
+def test_reconstructed_collision_lockstep_parity(name, make):
+    """eq. reconstructedCollision (Section 4.5): equilibria averaged over each
+    leaf's reconstructed finest cells; meshes bit for bit, values within 1e-12."""
+    inst = make()
+    s = _solver(inst)
+    o = O.Oracle(params_of(inst))
+    for n in range(8):
+        R, vals, _ = gpu_state(s)
+        o.set_state(R, vals)
+        o.step()
+        s.advance(1)
+        R2, _, lvs = gpu_state(s)
+        assert np.array_equal(R2, o.get_state()[0]), f"step {n}: mesh differs"
+        assert_same_leaves(lvs, o)
+
+
+@pytest.mark.parametrize("name,make", RECOLL_CASES, ids=[c[0] for c in RECOLL_CASES])
+def test_reconstructed_collision_free_running_parity(name, make):
+    inst = make()
+    s = _solver(inst)
+    o = oracle_of(inst)
+    for n in range(25):
+        o.step()
+        s.advance(1)
+    R, _, lvs = gpu_state(s)
+    assert np.array_equal(R, o.get_state()[0])
+    assert_same_leaves(lvs, o, tol=1e-11)
+    m, res = s.audit()
+    assert np.allclose(m, o.mass(), rtol=1e-12, atol=1e-13)
+
+
+def test_reconstructed_collision_fp32_and_mixed_batch():
+    """Both collisions, all schemes and stencils in one context (two kernel
+    variants, two launches), FP64 against the oracle and FP32 within 1e-4."""
+    kinds = [(W.EQ_BURGERS, 1, RC), (W.EQ_EULER, 1, 0), (W.EQ_SW_D1Q5, 1, RC), (W.EQ_SW, 2, 0),
+             (W.EQ_ADVECTION, 1, RC), (W.EQ_SW_D1Q3, 1, 0), (W.EQ_EULER, 3, RC), (W.EQ_BURGERS, 1, 0)]
+    insts = [W.random_smooth(8 + (j % 3), eq, seed=140 + j, eps=1e-4, bc=j % 2).with_(gamma=g, collision=c)
+             for j, (eq, g, c) in enumerate(kinds)]
+    s64, s32 = _solver(insts), _solver(insts, precision=MR_FP32_MIXED)
+    s64.advance(10)
+    s32.advance(10)
+    for i in range(len(insts)):
+        o = oracle_of(insts[i])
+        o.step(10)
+        R, _, lvs = gpu_state(s64, i)
+        assert np.array_equal(R, o.get_state()[0]), i
+        assert_same_leaves(lvs, o, tol=1e-11)
+        err = insts[i].dx * np.abs(s32.finest(i) - o.finest_moments()).sum(axis=1)
+        assert np.all(err < 1e-4), (i, err)
