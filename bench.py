@@ -58,7 +58,7 @@ def source_hash() -> str:
     return h.hexdigest()[:16]
 
 
-def profiled_traffic(workload: str, precision: str, steps: int, warmup: int, instances: int):
+def profiled_traffic(workload: str, precision: str, graph_steps: int, instances: int):
     """DRAM bytes per launch from the committed ncu record (profiles/traffic.json),
     if it was taken on the current kernel source and the same launch (else None)."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
@@ -66,9 +66,9 @@ def profiled_traffic(workload: str, precision: str, steps: int, warmup: int, ins
         with open(path) as fh:
             j = json.load(fh)
         e = j[f"{workload}:{precision}"]
-        if e.get("source_hash") != source_hash() or e.get("steps") != steps or e.get("warmup") != warmup:
+        if e.get("source_hash") != source_hash() or e.get("graph_steps") != graph_steps:
             return None
-        if workload == "batch" and instances != 4096:
+        if e.get("instances") != instances:
             return None
         return e
     except Exception:
@@ -458,7 +458,7 @@ def main():
 
     def roof(r, prec):
         achieved = r["bytes_alg"] / r["dt"] / 1e9
-        tr = profiled_traffic(args.workload, prec, args.steps, args.warmup, len(insts))
+        tr = profiled_traffic(args.workload, prec, r["graph_steps"], len(insts))
         return {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
                 "traffic": (tr["dram_bytes_per_launch"] if tr else None),
                 "peak_source": f"{hbm_src} HBM copy bandwidth (MEASURED_PEAKS.json)" if hbm_src == "measured"
