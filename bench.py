@@ -459,10 +459,15 @@ def main():
     def roof(r, prec):
         achieved = r["bytes_alg"] / r["dt"] / 1e9
         tr = profiled_traffic(args.workload, prec, r["graph_steps"], len(insts))
-        return {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+        out = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
                 "traffic": (tr["dram_bytes_per_launch"] if tr else None),
+                "traffic_unit": f"DRAM bytes per launch ({r['graph_steps']} steps of every instance), ncu",
                 "peak_source": f"{hbm_src} HBM copy bandwidth (MEASURED_PEAKS.json)" if hbm_src == "measured"
                 else "fallback 6.8 TB/s", "algorithmic_bytes_per_update": 2 * r["qmean"] * (4 if prec == "fp32" else 8)}
+        if tr and "fp64_pipe_active_pct" in tr:
+            # GB300's FP64 units are the other roof of this kernel (two FP64 operations per SM per cycle)
+            out["fp64_pipe_active_pct"] = tr["fp64_pipe_active_pct"]
+        return out
 
     line = {
         "metric": METRIC, "value": head["updates"] / head["dt"], "unit": UNIT, "n_gpus": world,
