@@ -197,6 +197,18 @@ def oracle_throughput(insts, target_s: float = 15.0, warm: int = 4):
 
 # --------------------------------------------------------------------------- GPU leg
 
+def reduce_over_ranks(dt: float, upd: float, dist, device):
+    """Weak scaling: the job's time is the slowest rank's, its work the sum of
+    the ranks' leaf updates (every rank advances its own batch)."""
+    import torch
+
+    t = torch.tensor([dt, float(upd)], dtype=torch.float64, device=device)
+    tmax, tsum = t[:1].clone(), t[1:].clone()
+    dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
+    dist.all_reduce(tsum, op=dist.ReduceOp.SUM)
+    return float(tmax[0]), float(tsum[0])
+
+
 def run_gpu(insts, precision: int, steps: int, warmup: int, rank: int, world: int, dist, block=None):
     import numpy as np
     import torch
@@ -241,11 +253,7 @@ def run_gpu(insts, precision: int, steps: int, warmup: int, rank: int, world: in
     qmean = float((q * nleaf).sum() / max(1, nleaf.sum()))
     vb = 4 if precision == 1 else 8
     if dist:
-        t = torch.tensor([dt, float(upd), t_wall], dtype=torch.float64, device="cuda")
-        tm = t.clone()
-        dist.all_reduce(tm[:1], op=dist.ReduceOp.MAX)
-        dist.all_reduce(tm[1:2], op=dist.ReduceOp.SUM)
-        dt, upd = float(tm[0]), float(tm[1])
+        dt, upd = reduce_over_ranks(dt, upd, dist, "cuda")
     res = {
         "solver": s, "dt": dt, "updates": upd, "launches": launches, "clocks": clk.summary(), "tune": tune,
         "graph_steps": G,
