@@ -593,3 +593,36 @@ def test_reconstructed_collision_fp32_and_mixed_batch():
         assert_same_leaves(lvs, o, tol=1e-11)
         err = insts[i].dx * np.abs(s32.finest(i) - o.finest_moments()).sum(axis=1)
         assert np.all(err < 1e-4), (i, err)
+
+
+@pytest.mark.parametrize("precision", [MR_FP64, MR_FP32_MIXED])
+def test_full_batch_in_the_benchmark_launch_configuration(precision):
+    """The 4096-instance batch at full size, in the benchmark's configuration
+    (autotuned launch shape, a CUDA graph holding one 64-step persistent launch,
+    replayed): sampled instances against the oracle after 64 steps — meshes bit
+    for bit in FP64, FP32 within 1e-4 (L1) of the oracle's conserved moments."""
+    import torch
+
+    insts = W.batch(n=4096, seed=12163)
+    from paper_2102_12163_gb300 import MRLBM
+
+    s = MRLBM(insts, precision=precision)
+    s.set_initial()
+    s.autotune(8)
+    g = s.capture(32)
+    with torch.cuda.stream(s.stream):
+        g.replay()
+        g.replay()
+    s.sync()
+    for i in (0, 1365, 2730, 4095):
+        o = oracle_of(insts[i])
+        o.step(64)
+        if precision == MR_FP64:
+            R, _, lvs = gpu_state(s, i)
+            assert np.array_equal(R, o.get_state()[0]), i
+            assert_same_leaves(lvs, o, tol=1e-11)
+        else:
+            err = insts[i].dx * np.abs(s.finest(i) - o.finest_moments()).sum(axis=1)
+            assert np.all(err < 1e-4), (i, err)
+    upd, steps, _ = s.stats()
+    assert steps == 64 and upd > 0
