@@ -213,6 +213,25 @@ __device__ __forceinline__ void level_of_word(const TeamSmem<T> &sm, int g, int 
 // ---------------------------------------------------------------------------
 // scheme: vectorial D1Q2^n (Section 2.1, equilibria of Sections 5.1 and 5.3)
 
+// x * 2^k, bit for bit the correctly rounded product, in integer arithmetic
+// where the exponent field allows (normal operand and result) and with the
+// multiply otherwise: GB300's FP64 units are scarce, integer units are not.
+__device__ __forceinline__ double scale2(double x, int k) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    const int e = (int)((b >> 52) & 0x7FFull);
+    if (e > 0 && e < 0x7FF && e + k > 0 && e + k < 0x7FF)
+        return __longlong_as_double((long long)(b + ((unsigned long long)(long long)k << 52)));
+    return x * ldexp(1.0, k);
+}
+__device__ __forceinline__ float scale2(float x, int k) { return x * ldexpf(1.0f, k); }
+template <typename T>
+__device__ __forceinline__ T half_of(T x) {
+    if constexpr (sizeof(T) == 8)
+        return scale2(x, -1);
+    else
+        return T(0.5) * x;
+}
+
 template <typename T, int NF>
 __device__ __forceinline__ void equilibria(int eq, T eqp, const T *mc, T *meq) {
     using A = Ar<T>;
@@ -220,7 +239,7 @@ __device__ __forceinline__ void equilibria(int eq, T eqp, const T *mc, T *meq) {
         if (eq == 0)
             meq[0] = A::mul(eqp, mc[0]);  // advection: c m0
         else
-            meq[0] = A::mul(T(0.5), A::mul(mc[0], mc[0]));  // Burgers: m0^2 / 2
+            meq[0] = half_of<T>(A::mul(mc[0], mc[0]));  // Burgers: m0^2 / 2
     } else if constexpr (NF == 2) {
         // shallow water (h, hu): hu, hu^2 / h + g h^2 / 2
         meq[0] = mc[1];
@@ -252,9 +271,10 @@ __device__ __forceinline__ void collide(const InstDesc &d, T *f) {
     for (int i = 0; i < NF; ++i) {
         T s = (T)d.s[i];
         T mstar = A::add(A::mul(A::sub(T(1), s), mn[i]), A::mul(s, meq[i]));
-        T g = A::div(mstar, lam);
-        f[2 * i] = A::mul(T(0.5), A::add(mc[i], g));
-        f[2 * i + 1] = A::mul(T(0.5), A::sub(mc[i], g));
+        // m*/lambda: an exact power-of-two scaling when lambda = 2^k (same value as the division)
+        T g = d.lam_log2 != NOT_POW2 ? scale2(mstar, -d.lam_log2) : A::div(mstar, lam);
+        f[2 * i] = half_of<T>(A::add(mc[i], g));
+        f[2 * i + 1] = half_of<T>(A::sub(mc[i], g));
     }
 }
 
@@ -571,7 +591,7 @@ struct Worker {
                 if (h < q) c[h] = *reinterpret_cast<const typename V2<T>::type *>(row(h, l + 1) + 2 * k);
 #pragma unroll
             for (int h = 0; h < QMAX; ++h)
-                if (h < q) row(h, l)[k] = T(0.5) * (c[h].x + c[h].y);
+                if (h < q) row(h, l)[k] = half_of<T>(c[h].x + c[h].y);
         }
     }
 
@@ -710,9 +730,9 @@ struct Worker {
                     const T mc = A::add(f[2 * j], f[2 * j + 1]), mn = A::mul(lam, A::sub(f[2 * j], f[2 * j + 1]));
                     const T sj = (T)d.s[j];
                     const T mstar = A::add(A::mul(A::sub(T(1), sj), mn), A::mul(sj, mavg[j]));
-                    const T g = A::div(mstar, lam);
-                    f[2 * j] = A::mul(T(0.5), A::add(mc, g));
-                    f[2 * j + 1] = A::mul(T(0.5), A::sub(mc, g));
+                    const T g = d.lam_log2 != NOT_POW2 ? scale2(mstar, -d.lam_log2) : A::div(mstar, lam);
+                    f[2 * j] = half_of<T>(A::add(mc, g));
+                    f[2 * j + 1] = half_of<T>(A::sub(mc, g));
                 }
             }
 #pragma unroll

@@ -11,6 +11,7 @@
 // counterpart; it is a deployment convenience.
 #include <cuda_runtime.h>
 
+#include <cmath>
 #include <cstdint>
 #include <cstdio>
 #include <cstring>
@@ -119,6 +120,12 @@ extern "C" mr_status mr_run_static(const mr_instance_desc *desc, int precision, 
     h.mu_bar = d.mu_bar;
     h.gamma = d.gamma;
     h.collision = d.collision;
+    h.lam_log2 = NOT_POW2;
+    {
+        int e2 = 0;
+        const double fr = std::frexp(d.lambda, &e2);  // lambda = fr 2^e2, fr in [0.5, 1)
+        if (fr == 0.5 && e2 - 1 >= -16 && e2 - 1 <= 16) h.lam_log2 = e2 - 1;
+    }
     h.Wtot = W;
     h.eps = d.eps;
     h.a = d.a;
