@@ -1224,8 +1224,10 @@ struct Worker {
             return;
         }
         if constexpr (WIDE) {
-            reconstruct_wide();
-            return;
+            if (d.gamma > 1) {
+                reconstruct_wide();
+                return;
+            }
         }
         const uint32_t *R = mask(sm.cur);
         const uint32_t *leaves = list(L_LEAF);
@@ -1320,13 +1322,11 @@ struct Worker {
                     rfirst = rlast = row(h, l)[k];
                 } else {
                     if (need_first)
-                        rfirst = g == 1   ? edge_walk<T, 1, false>(rb, d.Jmin, d.Jmax, d.bc, R, sm.woff, c, l, k)
-                                 : g == 2 ? edge_walk<T, 2, false>(rb, d.Jmin, d.Jmax, d.bc, R, sm.woff, c, l, k)
-                                          : edge_walk<T, 3, false>(rb, d.Jmin, d.Jmax, d.bc, R, sm.woff, c, l, k);
+                        rfirst = g == 2 ? edge_walk<T, 2, false>(rb, d.Jmin, d.Jmax, d.bc, R, sm.woff, c, l, k)
+                                        : edge_walk<T, 3, false>(rb, d.Jmin, d.Jmax, d.bc, R, sm.woff, c, l, k);
                     if (need_last)
-                        rlast = g == 1   ? edge_walk<T, 1, true>(rb, d.Jmin, d.Jmax, d.bc, R, sm.woff, c, l, k)
-                                : g == 2 ? edge_walk<T, 2, true>(rb, d.Jmin, d.Jmax, d.bc, R, sm.woff, c, l, k)
-                                         : edge_walk<T, 3, true>(rb, d.Jmin, d.Jmax, d.bc, R, sm.woff, c, l, k);
+                        rlast = g == 2 ? edge_walk<T, 2, true>(rb, d.Jmin, d.Jmax, d.bc, R, sm.woff, c, l, k)
+                                       : edge_walk<T, 3, true>(rb, d.Jmin, d.Jmax, d.bc, R, sm.woff, c, l, k);
                 }
                 T *ph = Phi + (long long)h * (d.N + 1);
                 if (plus) {
