@@ -219,8 +219,8 @@ mr_status mr_reconstruction_coefficients(int dj, int kind, double *out);
 /* Tracing: SM clock cycles spent by instance inst in each phase of the step,
  * accumulated since its initial state, in the order
  *   projection (adapt), details + threshold, enlargement, grading + marking,
- *   grading of the levels of at most 32 cells, list counts + scan, list
- *   writes, data transfer, collision, projection (step), ghosts,
+ *   grading of the levels of at most 32 cells, reserved (zero), list
+ *   compaction, data transfer, collision, projection (step), ghosts,
  *   reconstruction, stream + audit
  * (n >= 13 slots).  Only a library compiled with MRG_PHASE_TIMERS records
  * them; otherwise the cycles are zero and MR_ERR_STATE is returned. */

@@ -68,7 +68,7 @@ _lib = None
 
 
 PHASES = ["projection (adapt)", "details + threshold", "enlargement", "grading + marking",
-          "grading (small levels)", "list counts + scan", "list writes", "data transfer", "collision",
+          "grading (small levels)", "reserved", "list compaction", "data transfer", "collision",
           "projection (step)", "ghosts", "reconstruction", "stream + audit"]
 
 
