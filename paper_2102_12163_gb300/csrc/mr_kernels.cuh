@@ -1009,9 +1009,65 @@ struct Worker {
             sync();
         }
         tick(T_GRADE);
-        if (tid == 0)
-            for (int l = d.Jmax < 5 ? d.Jmax : 5; l >= d.Jmin; --l) small_level(Rn, Ro, l, grade);
+        if (tid == 0) small_levels(Rn, Ro, grade);
         sync();
+    }
+
+    // The levels of at most 32 cells (one word each), coarsest last, by one
+    // thread: grading of level l-1 and the marks of level l as in the word-wise
+    // sweep, with the words of the level below kept in registers rather than
+    // reloaded after the previous level wrote them.
+    __device__ void small_levels(uint32_t *Rn, const uint32_t *Ro, bool grade) {
+        const int gam = WIDE ? d.gamma : 1;
+        uint32_t *LF = mask(M_LEAF), *PR = mask(M_PRED), *GH = mask(M_GH);
+        const int ltop = d.Jmax < 5 ? d.Jmax : 5;
+        // words of level ltop + 1 (two words when it has 64 cells, one when fewer)
+        uint32_t rc0 = 0u, rc1 = 0u, pc0 = 0u, pc1 = 0u, gc0 = 0u, gc1 = 0u;
+        if (ltop < d.Jmax) {
+            const int oc = sm.woff[ltop + 1];
+            rc0 = Rn[oc];
+            pc0 = PR[oc];
+            gc0 = GH[oc];
+            if (ltop + 1 >= 6) {
+                rc1 = Rn[oc + 1];
+                pc1 = PR[oc + 1];
+                gc1 = GH[oc + 1];
+            }
+        }
+        uint32_t r = Rn[sm.woff[ltop]];
+        for (int l = ltop; l >= d.Jmin; --l) {
+            const int n = 1 << l, o = sm.woff[l];
+            const uint32_t vb = n == 32 ? 0xFFFFFFFFu : ((1u << n) - 1u);
+            const uint32_t ro = Ro[o];
+            uint32_t rp = l > d.Jmin ? Rn[sm.woff[l - 1]] : 0u;
+            if (grade && l > d.Jmin + 1) {
+                const int np = n >> 1;
+                const uint32_t vbp = (1u << np) - 1u;
+                rp |= pairexpand(dil_small(fold2(r, 0u), np, gam)) & vbp;
+            }
+            uint32_t lf = r, pr, gh = 0u;
+            if (l < d.Jmax) {
+                lf = r & ~fold2(rc0, rc1);
+                pr = (lf | dil_small(fold2(pc0, pc1), n, gam)) & ~ro;
+                gh = (dil_small(lf, n, 2 * gam) | dil_small(fold2(gc0, gc1), n, gam)) & ~r;
+            } else {
+                pr = lf & ~ro;
+            }
+            lf &= vb;
+            pr &= vb;
+            gh &= vb;
+            LF[o] = lf;
+            PR[o] = pr;
+            GH[o] = gh;
+            if (l > d.Jmin) Rn[sm.woff[l - 1]] = rp;
+            rc0 = r;
+            rc1 = 0u;
+            pc0 = pr;
+            pc1 = 0u;
+            gc0 = gh;
+            gc1 = 0u;
+            r = rp;
+        }
     }
 
     // dilation by r cells inside a level of n <= 32 cells held in one word
@@ -1032,34 +1088,6 @@ struct Worker {
     // parent bits (n of them) of the child level l+1 of a level of n <= 32 cells
     __device__ __forceinline__ uint32_t fold_small(const uint32_t *child, int l) const {
         return l + 1 >= 6 ? fold2(child[0], child[1]) : fold2(child[0], 0u);
-    }
-
-    // one level of at most 32 cells (a single word): grading of level l-1 and
-    // marks of level l, as in the word-wise sweep above
-    __device__ void small_level(uint32_t *Rn, const uint32_t *Ro, int l, bool grade) {
-        const int gam = WIDE ? d.gamma : 1;
-        uint32_t *LF = mask(M_LEAF), *PR = mask(M_PRED), *GH = mask(M_GH);
-        const int n = 1 << l, o = sm.woff[l];
-        const uint32_t vb = n == 32 ? 0xFFFFFFFFu : ((1u << n) - 1u);
-        const uint32_t r = Rn[o];
-        if (grade && l > d.Jmin + 1) {
-            const int np = n >> 1;
-            const uint32_t vbp = (1u << np) - 1u;
-            Rn[sm.woff[l - 1]] |= pairexpand(dil_small(fold2(r, 0u), np, gam)) & vbp;
-        }
-        const uint32_t ro = Ro[o];
-        uint32_t lf = r, pr, gh = 0u;
-        if (l < d.Jmax) {
-            const int oc = sm.woff[l + 1];
-            lf = r & ~fold_small(Rn + oc, l);
-            pr = (lf | dil_small(fold_small(PR + oc, l), n, gam)) & ~ro;
-            gh = (dil_small(lf, n, 2 * gam) | dil_small(fold_small(GH + oc, l), n, gam)) & ~r;
-        } else {
-            pr = lf & ~ro;
-        }
-        LF[o] = lf & vb;
-        PR[o] = pr & vb;
-        GH[o] = gh & vb;
     }
 
     // ---- A5: list compaction -------------------------------------------------
