@@ -224,7 +224,9 @@ def run_gpu(insts, precision: int, steps: int, warmup: int, rank: int, world: in
     # restored afterwards) unless fixed
     G = GRAPH_STEPS if steps % GRAPH_STEPS == 0 else steps
     tune = s.autotune(G) if block is None else {"block": block, "fixed": True}
+    l0 = s.launches()
     graph = s.capture(G)
+    kernels_per_graph = s.launches() - l0  # one kernel per variant group the batch holds
     u0, _, _ = s.stats()
     ev0 = torch.cuda.Event(enable_timing=True)
     ev1 = torch.cuda.Event(enable_timing=True)
@@ -242,7 +244,7 @@ def run_gpu(insts, precision: int, steps: int, warmup: int, rank: int, world: in
     torch.cuda.synchronize()
     s.sync()
     dt = ev0.elapsed_time(ev1) / 1e3
-    launches = steps // G  # one kernel node per graph replay
+    launches = (steps // G) * kernels_per_graph
     u1, _, _ = s.stats()
     upd = u1 - u0
     q = np.array([i.q for i in insts], dtype=np.float64)
@@ -256,7 +258,7 @@ def run_gpu(insts, precision: int, steps: int, warmup: int, rank: int, world: in
         dt, upd = reduce_over_ranks(dt, upd, dist, "cuda")
     res = {
         "solver": s, "dt": dt, "updates": upd, "launches": launches, "clocks": clk.summary(), "tune": tune,
-        "graph_steps": G,
+        "graph_steps": G, "kernels_per_graph": kernels_per_graph,
         "bytes_alg": 2.0 * qmean * vb * upd, "qmean": qmean, "t_wall": t_wall,
     }
     return res
@@ -469,7 +471,8 @@ def main():
         tr = profiled_traffic(args.workload, prec, r["graph_steps"], len(insts))
         out = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
                 "traffic": (tr["dram_bytes_per_launch"] if tr else None),
-                "traffic_unit": f"DRAM bytes per launch ({r['graph_steps']} steps of every instance), ncu",
+                "traffic_unit": f"DRAM bytes per graph replay ({r['graph_steps']} steps of every instance, "
+                                f"{r['kernels_per_graph']} kernels), ncu",
                 "peak_source": f"{hbm_src} HBM copy bandwidth (MEASURED_PEAKS.json)" if hbm_src == "measured"
                 else "fallback 6.8 TB/s", "algorithmic_bytes_per_update": 2 * r["qmean"] * (4 if prec == "fp32" else 8)}
         if tr and "fp64_pipe_active_pct" in tr:
@@ -483,7 +486,8 @@ def main():
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32" if head_prec == "fp32" else "f64", "data": "synthetic",
         "config": {"workload": desc, "instances_per_gpu": len(insts), "steps_per_launch": head["graph_steps"],
-                   "launch": f"CUDA graph of one persistent launch of {head['graph_steps']} steps, replayed",
+                   "launch": f"CUDA graph of {head['graph_steps']} steps: one persistent launch per kernel "
+                             f"variant the batch needs ({head['kernels_per_graph']}, on forked streams), replayed",
                    "autotune": head["tune"],
                    "l2": "inputs larger than L2 (per-GPU workspace of several GB)",
                    "precision": "FP32 populations; FP64 detail test near the thresholds; mass audit in "

@@ -22,7 +22,11 @@
  *     must outlive the context's use; mr_destroy() does not free it.
  *   - Calls that launch work are asynchronous on the bound stream.  Errors found
  *     on the device (non-finite values) are reported by the next call that
- *     synchronises: mr_sync(), the getters, mr_stats().
+ *     synchronises: mr_sync(), the getters, mr_stats().  A batch whose
+ *     instances need more than one kernel variant (see mr_set_order) forks
+ *     part of a launch onto a stream the context owns and joins it back to
+ *     the bound stream before the call returns, by events; the pattern is
+ *     legal inside a stream capture, so a captured launch stays one graph.
  *   - Pointers marked "host or device" may be either (unified addressing);
  *     pointers marked "host" must be host memory.
  *   - The library is not thread-safe per context.
@@ -186,22 +190,28 @@ mr_status mr_stats(mr_ctx *ctx, unsigned long long *updates, unsigned long long 
  * Takes effect at the next launch. */
 mr_status mr_set_launch(mr_ctx *ctx, int block, int grid);
 
-/* Order in which the persistent launch's work queue hands out the instances:
- * by_fields = 1 (default) groups them by field count, largest first within a
- * group; 0 orders by size (nf 2^Jmax) alone.  Stream-ordered. */
+/* Order in which the persistent launches' work queues hand out the instances.
+ * The instances always form up to four groups, one per kernel variant: the
+ * fast variant (gamma = 1, leaves collision, two or more fields), the scalar
+ * variant (the same with one field, compiled for more resident blocks), the
+ * reconstructed-collision variant (gamma = 1) and the general variant (gamma =
+ * 2, 3, compiled for fewer resident blocks with more registers).  Within a
+ * group, by_fields = 1 (default) orders by scheme, largest first within a
+ * scheme; 0 orders by size (populations x 2^Jmax) alone.  Stream-ordered. */
 mr_status mr_set_order(mr_ctx *ctx, int by_fields);
 
 /* Autotuner of the batch driver (the paper has no counterpart).  Times nsteps
  * adaptive steps of the context's current state under each launch shape --
  * threads per block 128, 256, 512, 1024 (the cells of a level each block
- * sweeps per pass) times both queue orders of mr_set_order -- and keeps the
+ * sweeps per pass) with the queue order of mr_set_order -- and keeps the
  * fastest.  Before every trial, and once more at the end, the state is
  * restored from scratch: caller-owned device memory of at least
  * mr_workspace_size bytes, which receives a copy of the workspace.  The
  * results are unchanged by the launch shape (every shape computes the same
  * values), so the state after the call equals the state before it.
  * Synchronises the stream; not for use during stream capture.  best_block,
- * best_order and best_ms (the fastest trial in milliseconds) may be NULL. */
+ * best_order (the order in use, as mr_set_order's by_fields) and best_ms (the
+ * fastest trial in milliseconds) may be NULL. */
 mr_status mr_autotune(mr_ctx *ctx, int nsteps, void *scratch, size_t scratch_bytes, int *best_block,
                       int *best_order, float *best_ms);
 

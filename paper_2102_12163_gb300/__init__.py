@@ -97,8 +97,9 @@ class MRLBM:
         capi.check(self.h, self.lib.mr_set_order(self.h, 1 if by_fields else 0))
 
     def autotune(self, nsteps: int = 8) -> dict:
-        """Time nsteps steps under every launch shape (block size x queue order)
-        and keep the fastest; the state is restored, so results are unchanged."""
+        """Time nsteps steps under every block size (with the current queue
+        order) and keep the fastest; the state is restored, so results are
+        unchanged."""
         import torch
 
         scratch = torch.empty(self.workspace_bytes, dtype=torch.uint8, device=self.device)
@@ -110,8 +111,9 @@ class MRLBM:
         return {"block": b.value, "order_by_fields": bool(o.value), "ms_per_trial": ms.value, "steps": nsteps}
 
     def capture(self, nsteps: int):
-        """A CUDA graph holding one persistent launch of nsteps adaptive steps on
-        this context's stream; ``replay()`` advances every instance by nsteps."""
+        """A CUDA graph holding the persistent launches of nsteps adaptive steps
+        (one per kernel variant the batch needs, forked from and joined back to
+        this context's stream); ``replay()`` advances every instance by nsteps."""
         import torch
 
         torch.cuda.synchronize(self.device)

@@ -72,10 +72,17 @@ void dq_inverse(int eq, double lambda, double inv[5][5]) {
 }
 
 int nwords_h(int l) { return l >= 5 ? (1 << (l - 5)) : 1; }
-// instances that need the general kernel variant
-bool general_of(const InstDesc &h) { return h.gamma > 1 || h.collision != 0; }
 // compiled scheme variant of the kernels: D1Q2^n by field count, D1Q3, D1Q5
 int variant_of(int eq) { return eq == MR_EQ_SW_D1Q3 ? 4 : eq == MR_EQ_SW_D1Q5 ? 5 : nfields_of(eq); }
+// kernel variant an instance runs in (batched: the scalar scheme has its own)
+int kind_of(const InstDesc &h, bool batched) {
+    if (h.gamma > 1) return K_GENERAL;
+    if (h.collision != 0) return K_RECOLL;
+    return batched && variant_of(h.eq) == 1 ? K_SCALAR : K_FAST;
+}
+// position of a kernel variant's group in the queue order (and launch order)
+const int kGroupKind[NKIND] = {K_FAST, K_SCALAR, K_RECOLL, K_GENERAL};
+int group_of(int kind) { return kind == K_FAST ? 0 : kind == K_SCALAR ? 1 : kind == K_RECOLL ? 2 : 3; }
 
 thread_local std::string g_create_error;
 
@@ -97,10 +104,15 @@ struct mr_ctx {
     size_t ws_bytes = 0;
     cudaStream_t stream = nullptr;
     bool bound = false, initialised = false;
-    int block = 0, grid = 0, grid_req = 0, sms = 0;
-    int mask_cap = 0;    // words per bitmask a block team keeps in shared memory
-    int wmax = 0;        // mask words of the largest instance
-    int n_narrow = 0;    // instances with gamma = 1 (first in the queue order)
+    int block = 0, grid_req = 0, sms = 0;
+    int grid[NKIND] = {};      // blocks per launch, by kernel variant (K_*)
+    int mask_cap[NKIND] = {};  // words per bitmask a block team keeps in shared memory, by variant
+    int wmax = 0;              // mask words of the largest instance
+    int n_group[NKIND] = {};   // instances per group of the queue order (kGroupKind)
+    // The groups run as separate kernels; a second stream lets one group's
+    // kernel fill the SMs that another's tail leaves idle (fork and join by events).
+    cudaStream_t side = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     bool order_by_fields = true;
     std::vector<int> order_host;  // staging of the queue order (kept alive for the async copy)
     long long launches = 0;
@@ -122,6 +134,11 @@ struct mr_ctx {
     bool fp32() const { return precision == MR_FP32_MIXED; }
     size_t vbytes() const { return fp32() ? 4 : 8; }
     int n() const { return (int)desc.size(); }
+    ~mr_ctx() {
+        if (ev_fork) cudaEventDestroy(ev_fork);
+        if (ev_join) cudaEventDestroy(ev_join);
+        if (side) cudaStreamDestroy(side);
+    }
 };
 
 // ---------------------------------------------------------------------------
@@ -292,42 +309,65 @@ static void make_tables(Tables<double> &td, Tables<float> &tf) {
         }
 }
 
-static int launch_group(mr_ctx *c, int phases, int nsteps, const int *order, int n, bool wide, const void *aux0,
-                        const void *aux1) {
+static int launch_group(mr_ctx *c, int phases, int nsteps, const int *order, int n, int kind, const void *aux0,
+                        const void *aux1, cudaStream_t stream) {
     LaunchArgs a{};
     a.descs = (const InstDesc *)(c->ws + c->off_desc);
     a.order = order;
     a.n = n;
-    a.wide = wide ? 1 : 0;
+    a.kind = kind;
     a.nsteps = nsteps;
     a.phases = phases;
-    a.queue = (int *)(c->ws + c->off_queue);
+    a.queue = (int *)(c->ws + c->off_queue) + 16 * kind;  // one counter per variant, 64 bytes apart
     a.aux0 = aux0;
     a.aux1 = aux1;
     a.tables = c->ws + c->off_tab + (c->fp32() ? sizeof(Tables<double>) : 0);
-    a.smem_mask_words = c->mask_cap;
-    int rc = c->cuda(cudaMemsetAsync(a.queue, 0, sizeof(int), c->stream), "cudaMemsetAsync");
+    a.smem_mask_words = c->mask_cap[kind];
+    int rc = c->cuda(cudaMemsetAsync(a.queue, 0, sizeof(int), stream), "cudaMemsetAsync");
     if (rc) return rc;
-    int grid = std::min(a.n, c->grid);
-    int e = mrg_launch(c->fp32(), c->block, std::max(grid, 1), a, c->stream);
+    int grid = std::min(a.n, c->grid[kind]);
+    int e = mrg_launch(c->fp32(), c->block, std::max(grid, 1), a, stream);
     ++c->launches;
     if (e) return c->cuda((cudaError_t)e, "kernel launch");
     return MR_OK;
 }
 
-// A launch over the instances: the queue order puts the instances of the fast
-// kernel variant (gamma = 1, leaves collision) first; the others run in the
-// general variant (wide stencils, reconstructed collision).
+// A launch over the instances.  The queue order holds up to four groups, each
+// run by its own kernel variant: the fast kernel (gamma = 1, leaves collision,
+// two or more fields), the scalar kernel (the same for one field), the
+// reconstructed-collision kernel (gamma = 1) and the general kernel (gamma =
+// 2, 3).  With more than one group the groups alternate between the context's
+// stream and a side stream that forks from it and joins it again, so the
+// launches overlap.
 static int launch(mr_ctx *c, int phases, int nsteps, int only_inst, const void *aux0, const void *aux1) {
     if (!c->bound) return c->fail(MR_ERR_STATE, "context not bound to a workspace");
-    if (only_inst >= 0)
-        return launch_group(c, phases, nsteps, (const int *)(c->ws + c->off_ident) + only_inst, 1,
-                            general_of(c->hdesc[only_inst]), aux0, aux1);
+    if (only_inst >= 0) {
+        const int kind = kind_of(c->hdesc[only_inst], false);
+        return launch_group(c, phases, nsteps, (const int *)(c->ws + c->off_ident) + only_inst, 1, kind, aux0, aux1,
+                            c->stream);
+    }
     const int *order = (const int *)(c->ws + c->off_order);
+    int groups = 0;
+    for (int g = 0; g < NKIND; ++g) groups += c->n_group[g] > 0;
+    const bool fork = groups > 1;
     int rc = MR_OK;
-    if (c->n_narrow > 0) rc = launch_group(c, phases, nsteps, order, c->n_narrow, false, aux0, aux1);
-    if (!rc && c->n_narrow < c->n())
-        rc = launch_group(c, phases, nsteps, order + c->n_narrow, c->n() - c->n_narrow, true, aux0, aux1);
+    if (fork) {
+        if ((rc = c->cuda(cudaEventRecord(c->ev_fork, c->stream), "cudaEventRecord"))) return rc;
+        if ((rc = c->cuda(cudaStreamWaitEvent(c->side, c->ev_fork, 0), "cudaStreamWaitEvent"))) return rc;
+    }
+    int first = 0, k = 0;
+    for (int g = 0; g < NKIND && !rc; ++g) {
+        if (c->n_group[g] == 0) continue;
+        cudaStream_t st = (fork && (k++ & 1)) ? c->side : c->stream;
+        rc = launch_group(c, phases, nsteps, order + first, c->n_group[g], kGroupKind[g], aux0, aux1, st);
+        first += c->n_group[g];
+    }
+    if (fork) {
+        // join even after a failed launch, so the side stream never outlives the caller's order
+        int rj = c->cuda(cudaEventRecord(c->ev_join, c->side), "cudaEventRecord");
+        if (!rj) rj = c->cuda(cudaStreamWaitEvent(c->stream, c->ev_join, 0), "cudaStreamWaitEvent");
+        if (!rc) rc = rj;
+    }
     return rc;
 }
 
@@ -448,29 +488,33 @@ mr_status mr_workspace_size(const mr_ctx *cc, size_t *bytes) {
 // instance may use most of the SM; a batch keeps several blocks resident), and
 // one wave of resident blocks unless the caller fixed the grid.
 static int configure(mr_ctx *c) {
-    // resident blocks the registers allow (64 per thread) share the SM's 227 KB
-    int by_regs = std::max(1, 65536 / (c->block * 64));
-    size_t budget = c->n() == 1 ? 220u * 1024u : (227u * 1024u) / (size_t)by_regs - 1024u;
-    size_t base = mrg_smem_bytes(c->fp32(), c->block, 0);
-    int fit = budget > base ? (int)((budget - base) / (NMASK * sizeof(uint32_t))) : 0;
-    c->mask_cap = std::min(c->wmax, fit);
-    int nb = 0;
-    int rc = c->cuda((cudaError_t)mrg_occupancy(c->fp32(), c->block, c->mask_cap, &nb), "occupancy");
-    if (rc) return rc;
-    c->grid = c->grid_req > 0 ? c->grid_req : std::max(1, nb) * c->sms;
+    const size_t base = mrg_smem_bytes(c->fp32(), c->block, 0);
+    for (int kind = 0; kind < NKIND; ++kind) {
+        // the resident blocks a variant is compiled for share the SM's 227 KB
+        const int minb = std::max(1, mrg_min_blocks(c->fp32(), c->block, kind));
+        size_t budget = c->n() == 1 ? 220u * 1024u : (227u * 1024u) / (size_t)minb - 1024u;
+        int fit = budget > base ? (int)((budget - base) / (NMASK * sizeof(uint32_t))) : 0;
+        c->mask_cap[kind] = std::min(c->wmax, fit);
+        int nb = 0;
+        int rc = c->cuda((cudaError_t)mrg_occupancy(c->fp32(), c->block, kind, c->mask_cap[kind], &nb), "occupancy");
+        if (rc) return rc;
+        c->grid[kind] = c->grid_req > 0 ? c->grid_req : std::max(1, nb) * c->sms;
+    }
     return MR_OK;
 }
 
-// Processing order of the work queue: by field count first (blocks resident
-// together then run the same scheme's code, which keeps the instruction cache
-// warm) unless disabled, then largest first (nf 2^Jmax as the cost estimate).
+// Processing order of the work queue: by kernel variant group (fast, scalar,
+// general), then by field count (blocks resident together then run the same
+// scheme's code, which keeps the instruction cache warm) unless disabled, then
+// largest first (populations x 2^Jmax as the cost estimate).
 static int upload_order(mr_ctx *c) {
     const int n = c->n();
     const std::vector<InstDesc> &dd = c->hdesc;
     std::vector<int> order(n);
     for (int i = 0; i < n; ++i) order[i] = i;
     std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
-        if (general_of(dd[x]) != general_of(dd[y])) return !general_of(dd[x]);  // kernel variant groups
+        const int gx = group_of(kind_of(dd[x], true)), gy = group_of(kind_of(dd[y], true));
+        if (gx != gy) return gx < gy;  // kernel variant groups
         const int vx = variant_of(dd[x].eq), vy = variant_of(dd[y].eq);
         if (c->order_by_fields && vx != vy) return vx > vy;
         double cx = (double)npop_of(dd[x].eq) * std::ldexp(1.0, dd[x].Jmax);
@@ -478,8 +522,8 @@ static int upload_order(mr_ctx *c) {
         return cx > cy;
     });
     c->order_host = order;
-    c->n_narrow = 0;
-    for (int i = 0; i < n; ++i) c->n_narrow += !general_of(dd[i]);
+    for (int g = 0; g < NKIND; ++g) c->n_group[g] = 0;
+    for (int i = 0; i < n; ++i) ++c->n_group[group_of(kind_of(dd[i], true))];
     return c->cuda(cudaMemcpyAsync(c->ws + c->off_order, c->order_host.data(), sizeof(int) * n, cudaMemcpyHostToDevice,
                                    c->stream),
                    "upload");
@@ -498,6 +542,12 @@ mr_status mr_bind(mr_ctx *c, void *ws, size_t bytes, void *stream) {
     int dev = 0;
     if ((rc = c->cuda(cudaGetDevice(&dev), "cudaGetDevice"))) return (mr_status)rc;
     if ((rc = c->cuda(cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, dev), "attribute"))) return (mr_status)rc;
+    if (!c->side) {
+        if ((rc = c->cuda(cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking), "cudaStreamCreateWithFlags")) ||
+            (rc = c->cuda(cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming), "cudaEventCreateWithFlags")) ||
+            (rc = c->cuda(cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming), "cudaEventCreateWithFlags")))
+            return (mr_status)rc;
+    }
     // descriptors with absolute pointers
     int n = c->n();
     std::vector<InstDesc> dd = c->hdesc;
@@ -835,47 +885,43 @@ mr_status mr_autotune(mr_ctx *c, int nsteps, void *scratch, size_t scratch_bytes
         cudaEventDestroy(e0);
         return (mr_status)rc;
     }
+    // Only the block size is tuned.  The queue order is not: a trial's 64 steps
+    // right after the initial state timed both orders alike on the mixed batch,
+    // while over a thousand steps the order by scheme ran 7 % faster.
     const int blocks[4] = {128, 256, 512, 1024};
-    const int norders = c->n() > 1 ? 2 : 1;
     const int block0 = c->block, grid0 = c->grid_req;
-    const bool order0 = c->order_by_fields;
-    int bb = block0, bo = order0 ? 1 : 0;
+    int bb = block0;
     float bt = -1.0f;
     auto restore = [&]() { return c->cuda(cudaMemcpyAsync(c->ws, scratch, c->total, cudaMemcpyDeviceToDevice, s), "restore"); };
-    for (int ib = 0; ib < 4 && !rc; ++ib)
-        for (int io = 0; io < norders && !rc; ++io) {
-            c->block = blocks[ib];
-            c->grid_req = 0;
-            c->order_by_fields = norders == 1 ? order0 : io == 0;
-            if ((rc = configure(c)) || (rc = upload_order(c))) break;
-            // untimed step first (first launch of a block size sets its attributes), then the trial
-            if ((rc = restore()) || (rc = launch(c, PH_ADAPT | PH_STEP, 1, -1, nullptr, nullptr)) || (rc = restore())) break;
-            if ((rc = c->cuda(cudaEventRecord(e0, s), "cudaEventRecord"))) break;
-            if ((rc = launch(c, PH_ADAPT | PH_STEP, nsteps, -1, nullptr, nullptr))) break;
-            if ((rc = c->cuda(cudaEventRecord(e1, s), "cudaEventRecord"))) break;
-            if ((rc = c->cuda(cudaEventSynchronize(e1), "cudaEventSynchronize"))) break;
-            float ms = 0.0f;
-            if ((rc = c->cuda(cudaEventElapsedTime(&ms, e0, e1), "cudaEventElapsedTime"))) break;
-            if (bt < 0.0f || ms < bt) {
-                bt = ms;
-                bb = c->block;
-                bo = c->order_by_fields ? 1 : 0;
-            }
+    for (int ib = 0; ib < 4 && !rc; ++ib) {
+        c->block = blocks[ib];
+        c->grid_req = 0;
+        if ((rc = configure(c))) break;
+        // untimed step first (first launch of a block size sets its attributes), then the trial
+        if ((rc = restore()) || (rc = launch(c, PH_ADAPT | PH_STEP, 1, -1, nullptr, nullptr)) || (rc = restore())) break;
+        if ((rc = c->cuda(cudaEventRecord(e0, s), "cudaEventRecord"))) break;
+        if ((rc = launch(c, PH_ADAPT | PH_STEP, nsteps, -1, nullptr, nullptr))) break;
+        if ((rc = c->cuda(cudaEventRecord(e1, s), "cudaEventRecord"))) break;
+        if ((rc = c->cuda(cudaEventSynchronize(e1), "cudaEventSynchronize"))) break;
+        float ms = 0.0f;
+        if ((rc = c->cuda(cudaEventElapsedTime(&ms, e0, e1), "cudaEventElapsedTime"))) break;
+        if (bt < 0.0f || ms < bt) {
+            bt = ms;
+            bb = c->block;
         }
+    }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     // the fastest shape (the caller's on failure) and the saved state
     c->block = rc ? block0 : bb;
     c->grid_req = rc ? grid0 : 0;
-    c->order_by_fields = rc ? order0 : bo != 0;
     int rc2 = configure(c);
-    if (!rc2) rc2 = upload_order(c);
     if (!rc2) rc2 = restore();
     if (!rc2) rc2 = c->cuda(cudaStreamSynchronize(s), "cudaStreamSynchronize");
     if (rc) return (mr_status)rc;
     if (rc2) return (mr_status)rc2;
     if (best_block) *best_block = bb;
-    if (best_order) *best_order = bo;
+    if (best_order) *best_order = c->order_by_fields ? 1 : 0;
     if (best_ms) *best_ms = bt;
     return MR_OK;
 }

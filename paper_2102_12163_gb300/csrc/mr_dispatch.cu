@@ -3,85 +3,60 @@
 
 #include "mr_common.h"
 
-int mrg_launch_f64_128(int, const mrg::LaunchArgs &, cudaStream_t);
-int mrg_occ_f64_128(int, int *);
-size_t mrg_smem_f64_128(int);
-int mrg_launch_f64_256(int, const mrg::LaunchArgs &, cudaStream_t);
-int mrg_occ_f64_256(int, int *);
-size_t mrg_smem_f64_256(int);
-int mrg_launch_f64_512(int, const mrg::LaunchArgs &, cudaStream_t);
-int mrg_occ_f64_512(int, int *);
-size_t mrg_smem_f64_512(int);
-int mrg_launch_f64_1024(int, const mrg::LaunchArgs &, cudaStream_t);
-int mrg_occ_f64_1024(int, int *);
-size_t mrg_smem_f64_1024(int);
-int mrg_launch_f32_128(int, const mrg::LaunchArgs &, cudaStream_t);
-int mrg_occ_f32_128(int, int *);
-size_t mrg_smem_f32_128(int);
-int mrg_launch_f32_256(int, const mrg::LaunchArgs &, cudaStream_t);
-int mrg_occ_f32_256(int, int *);
-size_t mrg_smem_f32_256(int);
-int mrg_launch_f32_512(int, const mrg::LaunchArgs &, cudaStream_t);
-int mrg_occ_f32_512(int, int *);
-size_t mrg_smem_f32_512(int);
-int mrg_launch_f32_1024(int, const mrg::LaunchArgs &, cudaStream_t);
-int mrg_occ_f32_1024(int, int *);
-size_t mrg_smem_f32_1024(int);
+#define MRG_DECLARE(TAG)                                        \
+    int mrg_launch_##TAG(int, const mrg::LaunchArgs &, cudaStream_t); \
+    int mrg_occ_##TAG(int, int, int *);                         \
+    int mrg_minb_##TAG(int);                                    \
+    size_t mrg_smem_##TAG(int);
+MRG_DECLARE(f64_128)
+MRG_DECLARE(f64_256)
+MRG_DECLARE(f64_512)
+MRG_DECLARE(f64_1024)
+MRG_DECLARE(f32_128)
+MRG_DECLARE(f32_256)
+MRG_DECLARE(f32_512)
+MRG_DECLARE(f32_1024)
+
+// CALL(TAG) is expanded for the instantiation of (fp32, block); FAIL otherwise.
+#define MRG_ROUTE(CALL, FAIL)                    \
+    if (fp32) {                                  \
+        switch (block) {                         \
+        case 128: return CALL(f32_128);          \
+        case 256: return CALL(f32_256);          \
+        case 512: return CALL(f32_512);          \
+        case 1024: return CALL(f32_1024);        \
+        }                                        \
+    } else {                                     \
+        switch (block) {                         \
+        case 128: return CALL(f64_128);          \
+        case 256: return CALL(f64_256);          \
+        case 512: return CALL(f64_512);          \
+        case 1024: return CALL(f64_1024);        \
+        }                                        \
+    }                                            \
+    return FAIL;
 
 int mrg_launch(bool fp32, int block, int grid, const mrg::LaunchArgs &a, void *stream) {
     cudaStream_t s = (cudaStream_t)stream;
-    if (fp32) {
-        switch (block) {
-        case 128: return mrg_launch_f32_128(grid, a, s);
-        case 256: return mrg_launch_f32_256(grid, a, s);
-        case 512: return mrg_launch_f32_512(grid, a, s);
-        case 1024: return mrg_launch_f32_1024(grid, a, s);
-        }
-    } else {
-        switch (block) {
-        case 128: return mrg_launch_f64_128(grid, a, s);
-        case 256: return mrg_launch_f64_256(grid, a, s);
-        case 512: return mrg_launch_f64_512(grid, a, s);
-        case 1024: return mrg_launch_f64_1024(grid, a, s);
-        }
-    }
-    return (int)cudaErrorInvalidValue;
+#define MRG_CALL(TAG) mrg_launch_##TAG(grid, a, s)
+    MRG_ROUTE(MRG_CALL, (int)cudaErrorInvalidValue)
+#undef MRG_CALL
 }
 
-int mrg_occupancy(bool fp32, int block, int mask_words, int *nb) {
-    if (fp32) {
-        switch (block) {
-        case 128: return mrg_occ_f32_128(mask_words, nb);
-        case 256: return mrg_occ_f32_256(mask_words, nb);
-        case 512: return mrg_occ_f32_512(mask_words, nb);
-        case 1024: return mrg_occ_f32_1024(mask_words, nb);
-        }
-    } else {
-        switch (block) {
-        case 128: return mrg_occ_f64_128(mask_words, nb);
-        case 256: return mrg_occ_f64_256(mask_words, nb);
-        case 512: return mrg_occ_f64_512(mask_words, nb);
-        case 1024: return mrg_occ_f64_1024(mask_words, nb);
-        }
-    }
-    return (int)cudaErrorInvalidValue;
+int mrg_occupancy(bool fp32, int block, int kind, int mask_words, int *nb) {
+#define MRG_CALL(TAG) mrg_occ_##TAG(kind, mask_words, nb)
+    MRG_ROUTE(MRG_CALL, (int)cudaErrorInvalidValue)
+#undef MRG_CALL
+}
+
+int mrg_min_blocks(bool fp32, int block, int kind) {
+#define MRG_CALL(TAG) mrg_minb_##TAG(kind)
+    MRG_ROUTE(MRG_CALL, 0)
+#undef MRG_CALL
 }
 
 size_t mrg_smem_bytes(bool fp32, int block, int mask_words) {
-    if (fp32) {
-        switch (block) {
-        case 128: return mrg_smem_f32_128(mask_words);
-        case 256: return mrg_smem_f32_256(mask_words);
-        case 512: return mrg_smem_f32_512(mask_words);
-        case 1024: return mrg_smem_f32_1024(mask_words);
-        }
-    } else {
-        switch (block) {
-        case 128: return mrg_smem_f64_128(mask_words);
-        case 256: return mrg_smem_f64_256(mask_words);
-        case 512: return mrg_smem_f64_512(mask_words);
-        case 1024: return mrg_smem_f64_1024(mask_words);
-        }
-    }
-    return 0;
+#define MRG_CALL(TAG) mrg_smem_##TAG(mask_words)
+    MRG_ROUTE(MRG_CALL, (size_t)0)
+#undef MRG_CALL
 }

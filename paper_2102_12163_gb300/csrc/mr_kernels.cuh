@@ -1832,7 +1832,7 @@ __device__ __forceinline__ void run_instance(TeamSmem<T> &sm, const Tables<T> &t
 // Bitmasks live in shared memory (smask, room for `cap` words per mask) when the
 // instance fits: the current tree is copied in at the start and back at the
 // end, KEEP / REF start cleared, the other masks are rebuilt by every step.
-template <typename T, int TS, bool WIDE>
+template <typename T, int TS, bool WIDE, bool SCALAR>
 __device__ void run_team(TeamSmem<T> &sm, const Tables<T> &tab, BlockScratch &bx, const LaunchArgs &a,
                          const InstDesc &dg, int tid, uint32_t *smask, int cap) {
     load_instance<T, TS>(sm, dg, tid);
@@ -1849,14 +1849,18 @@ __device__ void run_team(TeamSmem<T> &sm, const Tables<T> &tab, BlockScratch &bx
         }
         __syncthreads();
     }
-    // scheme variant: D1Q2^nf, or D1Q3 / D1Q5 shallow water (equilibria 4, 5)
-    const int var = sm.d.eq == 4 ? 4 : sm.d.eq == 5 ? 5 : sm.d.nf;
-    switch (var) {
-    case 1: run_instance<T, 1, TS, WIDE>(sm, tab, bx, a, tid, masks); break;
-    case 2: run_instance<T, 2, TS, WIDE>(sm, tab, bx, a, tid, masks); break;
-    case 4: run_instance<T, 4, TS, WIDE>(sm, tab, bx, a, tid, masks); break;
-    case 5: run_instance<T, 5, TS, WIDE>(sm, tab, bx, a, tid, masks); break;
-    default: run_instance<T, 3, TS, WIDE>(sm, tab, bx, a, tid, masks); break;
+    if constexpr (SCALAR) {
+        run_instance<T, 1, TS, WIDE>(sm, tab, bx, a, tid, masks);
+    } else {
+        // scheme variant: D1Q2^nf, or D1Q3 / D1Q5 shallow water (equilibria 4, 5)
+        const int var = sm.d.eq == 4 ? 4 : sm.d.eq == 5 ? 5 : sm.d.nf;
+        switch (var) {
+        case 1: run_instance<T, 1, TS, WIDE>(sm, tab, bx, a, tid, masks); break;
+        case 2: run_instance<T, 2, TS, WIDE>(sm, tab, bx, a, tid, masks); break;
+        case 4: run_instance<T, 4, TS, WIDE>(sm, tab, bx, a, tid, masks); break;
+        case 5: run_instance<T, 5, TS, WIDE>(sm, tab, bx, a, tid, masks); break;
+        default: run_instance<T, 3, TS, WIDE>(sm, tab, bx, a, tid, masks); break;
+        }
     }
     if (local) {
         uint32_t *gr = sm.d.masks + (long long)sm.cur * W;
@@ -1867,11 +1871,15 @@ __device__ void run_team(TeamSmem<T> &sm, const Tables<T> &tab, BlockScratch &bx
 }
 
 // Persistent kernel: each block takes instances from the queue (largest first)
-// and advances one at a time with all its threads.  WIDE: the instances of the
-// launch use prediction stencils gamma = 2 or 3 (a separate kernel, so the
-// gamma = 1 code is compiled on its own).
-template <typename T, int NT, int MINB, bool WIDE>
+// and advances one at a time with all its threads.  KIND selects the code the
+// kernel holds: K_FAST every scheme with gamma = 1 and the leaves collision;
+// K_GENERAL and K_RECOLL wide prediction stencils (gamma = 2, 3) and the
+// reconstructed collision; K_SCALAR the gamma = 1 code of the scalar D1Q2
+// scheme alone, whose smaller register footprint lets more blocks share an SM
+// (a larger MINB).
+template <typename T, int NT, int MINB, int KIND>
 __global__ void __launch_bounds__(NT, MINB) mr_persistent(LaunchArgs a) {
+    constexpr bool WIDE = KIND == K_GENERAL || KIND == K_RECOLL;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     BlockSmem<T, NT> &bs = *reinterpret_cast<BlockSmem<T, NT> *>(smem_raw);
     uint32_t *smask = a.smem_mask_words > 0
@@ -1888,7 +1896,7 @@ __global__ void __launch_bounds__(NT, MINB) mr_persistent(LaunchArgs a) {
         const int idx = bs.idx;
         __syncthreads();
         if (idx >= a.n) return;
-        run_team<T, NT, WIDE>(bs.team, bs.tab, bs.scratch, a, a.descs[a.order[idx]], threadIdx.x, smask,
+        run_team<T, NT, WIDE, KIND == K_SCALAR>(bs.team, bs.tab, bs.scratch, a, a.descs[a.order[idx]], threadIdx.x, smask,
                               a.smem_mask_words);
     }
 }
@@ -1896,34 +1904,56 @@ __global__ void __launch_bounds__(NT, MINB) mr_persistent(LaunchArgs a) {
 }  // namespace mrg
 
 // One translation unit per (precision, block size) instantiation keeps the
-// build parallel; mr_dispatch.cu routes a launch to the right one.
-#define MRG_INSTANTIATE(T, NT, MINB, TAG)                                                          \
+// build parallel; mr_dispatch.cu routes a launch to the right one.  MINB,
+// MINB_S and MINB_G are the resident blocks per SM the fast, scalar and
+// general kernels are compiled for (K_RECOLL takes MINB): the scalar code fits
+// in fewer registers, the wide-stencil code runs faster with more registers and
+// fewer resident blocks.
+#define MRG_INSTANTIATE(T, NT, MINB, MINB_S, MINB_G, TAG)                                          \
     static size_t mrg_dyn_##TAG(int mask_words) {                                                 \
         size_t base = (sizeof(mrg::BlockSmem<T, NT>) + 15) / 16 * 16;                              \
         return base + (size_t)mask_words * mrg::NMASK * sizeof(uint32_t);                          \
     }                                                                                             \
+    template <int M, int K>                                                                       \
+    static int mrg_allow_##TAG() {                                                                \
+        return (int)cudaFuncSetAttribute(mrg::mr_persistent<T, NT, M, K>,                         \
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024); \
+    }                                                                                             \
     static int mrg_attr_##TAG() {                                                                 \
-        static int rc = (int)cudaFuncSetAttribute(mrg::mr_persistent<T, NT, MINB, false>,         \
-                                                  cudaFuncAttributeMaxDynamicSharedMemorySize,     \
-                                                  227 * 1024) |                                    \
-                        (int)cudaFuncSetAttribute(mrg::mr_persistent<T, NT, MINB, true>,          \
-                                                  cudaFuncAttributeMaxDynamicSharedMemorySize,     \
-                                                  227 * 1024);                                     \
+        static int rc = mrg_allow_##TAG<MINB, mrg::K_FAST>() | mrg_allow_##TAG<MINB_G, mrg::K_GENERAL>() | \
+                        mrg_allow_##TAG<MINB_S, mrg::K_SCALAR>() | mrg_allow_##TAG<MINB, mrg::K_RECOLL>(); \
         return rc;                                                                                \
+    }                                                                                             \
+    template <int M, int K>                                                                       \
+    static int mrg_occ1_##TAG(size_t dyn, int *nb) {                                              \
+        return (int)cudaOccupancyMaxActiveBlocksPerMultiprocessor(nb, mrg::mr_persistent<T, NT, M, K>, NT, dyn); \
     }                                                                                             \
     int mrg_launch_##TAG(int grid, const mrg::LaunchArgs &a, cudaStream_t s) {                     \
         int rc = mrg_attr_##TAG();                                                                \
         if (rc) return rc;                                                                        \
-        if (a.wide)                                                                               \
-            mrg::mr_persistent<T, NT, MINB, true><<<grid, NT, mrg_dyn_##TAG(a.smem_mask_words), s>>>(a); \
-        else                                                                                      \
-            mrg::mr_persistent<T, NT, MINB, false><<<grid, NT, mrg_dyn_##TAG(a.smem_mask_words), s>>>(a); \
+        const size_t dyn = mrg_dyn_##TAG(a.smem_mask_words);                                       \
+        switch (a.kind) {                                                                         \
+        case mrg::K_FAST: mrg::mr_persistent<T, NT, MINB, mrg::K_FAST><<<grid, NT, dyn, s>>>(a); break; \
+        case mrg::K_GENERAL: mrg::mr_persistent<T, NT, MINB_G, mrg::K_GENERAL><<<grid, NT, dyn, s>>>(a); break; \
+        case mrg::K_SCALAR: mrg::mr_persistent<T, NT, MINB_S, mrg::K_SCALAR><<<grid, NT, dyn, s>>>(a); break; \
+        case mrg::K_RECOLL: mrg::mr_persistent<T, NT, MINB, mrg::K_RECOLL><<<grid, NT, dyn, s>>>(a); break; \
+        default: return (int)cudaErrorInvalidValue;                                               \
+        }                                                                                         \
         return (int)cudaGetLastError();                                                           \
     }                                                                                             \
-    int mrg_occ_##TAG(int mask_words, int *nb) {                                                  \
+    int mrg_occ_##TAG(int kind, int mask_words, int *nb) {                                        \
         int rc = mrg_attr_##TAG();                                                                \
         if (rc) return rc;                                                                        \
-        return (int)cudaOccupancyMaxActiveBlocksPerMultiprocessor(nb, mrg::mr_persistent<T, NT, MINB, false>, \
-                                                                   NT, mrg_dyn_##TAG(mask_words)); \
+        const size_t dyn = mrg_dyn_##TAG(mask_words);                                              \
+        switch (kind) {                                                                           \
+        case mrg::K_FAST: return mrg_occ1_##TAG<MINB, mrg::K_FAST>(dyn, nb);                       \
+        case mrg::K_GENERAL: return mrg_occ1_##TAG<MINB_G, mrg::K_GENERAL>(dyn, nb);               \
+        case mrg::K_SCALAR: return mrg_occ1_##TAG<MINB_S, mrg::K_SCALAR>(dyn, nb);                 \
+        case mrg::K_RECOLL: return mrg_occ1_##TAG<MINB, mrg::K_RECOLL>(dyn, nb);                   \
+        }                                                                                         \
+        return (int)cudaErrorInvalidValue;                                                        \
+    }                                                                                             \
+    int mrg_minb_##TAG(int kind) {                                                                \
+        return kind == mrg::K_SCALAR ? MINB_S : kind == mrg::K_GENERAL ? MINB_G : MINB;            \
     }                                                                                             \
     size_t mrg_smem_##TAG(int mask_words) { return mrg_dyn_##TAG(mask_words); }

@@ -173,7 +173,7 @@ extern "C" mr_status mr_run_static(const mr_instance_desc *desc, int precision, 
     a.queue = (int *)(base + oQueue);
     a.tables = base + oTab + (fp32 ? sizeof(Tables<double>) : 0);
     a.smem_mask_words = W <= fit ? W : 0;
-    a.wide = (d.gamma > 1 || d.collision != 0) ? 1 : 0;
+    a.kind = d.gamma > 1 ? K_GENERAL : d.collision != 0 ? K_RECOLL : K_FAST;
     const int phases[3] = {PH_INIT_FULL, PH_ADAPT | PH_STEP, PH_FINEST};
     const int steps[3] = {0, nsteps, 0};
     for (int i = 0; i < 3; ++i) {

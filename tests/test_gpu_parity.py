@@ -328,6 +328,31 @@ def test_graph_replay_equals_advance():
     assert a.stats() == b.stats()
 
 
+def test_graph_replay_of_every_kernel_variant_equals_advance():
+    """A captured launch over a batch that needs all four kernel variants (two
+    streams forked and joined inside the capture) replays to the same state as
+    plain launches."""
+    import torch
+
+    insts = _mixed_kinds_batch()
+    for prec in (MR_FP64, MR_FP32_MIXED):
+        a, b = _solver(insts, precision=prec), _solver(insts, precision=prec)
+        assert a.launches() == b.launches()
+        l0 = a.launches()
+        g = a.capture(3)
+        assert a.launches() - l0 == 4  # one kernel per variant group
+        with torch.cuda.stream(a.stream):
+            for _ in range(4):
+                g.replay()
+        b.advance(12)
+        a.sync()
+        b.sync()
+        for i in range(len(insts)):
+            assert np.array_equal(a.tree(i), b.tree(i)), (prec, i)
+            assert np.array_equal(a.leaves(i)[2], b.leaves(i)[2]), (prec, i)
+        assert a.stats() == b.stats()
+
+
 @pytest.mark.parametrize("test", ["I", "II", "III", "IV"])
 def test_scalar_tests_full_run_errors(test):
     """Tests I-IV of Table 1 run to their final time on the GPU: the FP64 path's
@@ -575,13 +600,22 @@ def test_reconstructed_collision_free_running_parity(name, make):
     assert np.allclose(m, o.mass(), rtol=1e-12, atol=1e-13)
 
 
+MIXED_KINDS = [(W.EQ_BURGERS, 1, RC), (W.EQ_EULER, 1, 0), (W.EQ_SW_D1Q5, 1, RC), (W.EQ_SW, 2, 0),
+               (W.EQ_ADVECTION, 1, RC), (W.EQ_SW_D1Q3, 1, 0), (W.EQ_EULER, 3, RC), (W.EQ_BURGERS, 1, 0)]
+
+
+def _mixed_kinds_batch():
+    """Every kernel variant in one batch: fast (several fields), scalar, gamma =
+    1 with the reconstructed collision, and gamma = 2, 3."""
+    return [W.random_smooth(8 + (j % 3), eq, seed=140 + j, eps=1e-4, bc=j % 2).with_(gamma=g, collision=c)
+            for j, (eq, g, c) in enumerate(MIXED_KINDS)]
+
+
 def test_reconstructed_collision_fp32_and_mixed_batch():
-    """Both collisions, all schemes and stencils in one context (two kernel
-    variants, two launches), FP64 against the oracle and FP32 within 1e-4."""
-    kinds = [(W.EQ_BURGERS, 1, RC), (W.EQ_EULER, 1, 0), (W.EQ_SW_D1Q5, 1, RC), (W.EQ_SW, 2, 0),
-             (W.EQ_ADVECTION, 1, RC), (W.EQ_SW_D1Q3, 1, 0), (W.EQ_EULER, 3, RC), (W.EQ_BURGERS, 1, 0)]
-    insts = [W.random_smooth(8 + (j % 3), eq, seed=140 + j, eps=1e-4, bc=j % 2).with_(gamma=g, collision=c)
-             for j, (eq, g, c) in enumerate(kinds)]
+    """Both collisions, all schemes and stencils in one context (four kernel
+    variants, four launches on two streams), FP64 against the oracle and FP32
+    within 1e-4."""
+    insts = _mixed_kinds_batch()
     s64, s32 = _solver(insts), _solver(insts, precision=MR_FP32_MIXED)
     s64.advance(10)
     s32.advance(10)
