@@ -487,7 +487,8 @@ def main():
         "dtype": "f32" if head_prec == "fp32" else "f64", "data": "synthetic",
         "config": {"workload": desc, "instances_per_gpu": len(insts), "steps_per_launch": head["graph_steps"],
                    "launch": f"CUDA graph of {head['graph_steps']} steps: one persistent launch per kernel "
-                             f"variant the batch needs ({head['kernels_per_graph']}, on forked streams), replayed",
+                             f"variant the batch needs ({head['kernels_per_graph']}"
+                             f"{', on forked streams' if head['kernels_per_graph'] > 1 else ''}), replayed",
                    "autotune": head["tune"],
                    "l2": "inputs larger than L2 (per-GPU workspace of several GB)",
                    "precision": "FP32 populations; FP64 detail test near the thresholds; mass audit in "

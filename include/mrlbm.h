@@ -191,13 +191,13 @@ mr_status mr_stats(mr_ctx *ctx, unsigned long long *updates, unsigned long long 
 mr_status mr_set_launch(mr_ctx *ctx, int block, int grid);
 
 /* Order in which the persistent launches' work queues hand out the instances.
- * The instances always form up to four groups, one per kernel variant: the
- * fast variant (gamma = 1, leaves collision, two or more fields), the scalar
- * variant (the same with one field, compiled for more resident blocks), the
- * reconstructed-collision variant (gamma = 1) and the general variant (gamma =
- * 2, 3, compiled for fewer resident blocks with more registers).  Within a
- * group, by_fields = 1 (default) orders by scheme, largest first within a
- * scheme; 0 orders by size (populations x 2^Jmax) alone.  Stream-ordered. */
+ * The instances always form up to three groups, each run by its own kernel
+ * variant: gamma = 2, 3 (compiled for fewer resident blocks with more
+ * registers), gamma = 1 with the reconstructed collision, and gamma = 1 with
+ * the leaves collision (a kernel compiled for more resident blocks when every
+ * instance of that group has one field).  Within a group, by_fields = 1
+ * (default) orders by scheme, largest first within a scheme; 0 orders by size
+ * (populations x 2^Jmax) alone.  Stream-ordered. */
 mr_status mr_set_order(mr_ctx *ctx, int by_fields);
 
 /* Autotuner of the batch driver (the paper has no counterpart).  Times nsteps

@@ -74,15 +74,12 @@ void dq_inverse(int eq, double lambda, double inv[5][5]) {
 int nwords_h(int l) { return l >= 5 ? (1 << (l - 5)) : 1; }
 // compiled scheme variant of the kernels: D1Q2^n by field count, D1Q3, D1Q5
 int variant_of(int eq) { return eq == MR_EQ_SW_D1Q3 ? 4 : eq == MR_EQ_SW_D1Q5 ? 5 : nfields_of(eq); }
-// kernel variant an instance runs in (batched: the scalar scheme has its own)
-int kind_of(const InstDesc &h, bool batched) {
-    if (h.gamma > 1) return K_GENERAL;
-    if (h.collision != 0) return K_RECOLL;
-    return batched && variant_of(h.eq) == 1 ? K_SCALAR : K_FAST;
-}
-// position of a kernel variant's group in the queue order (and launch order)
-const int kGroupKind[NKIND] = {K_FAST, K_SCALAR, K_RECOLL, K_GENERAL};
-int group_of(int kind) { return kind == K_FAST ? 0 : kind == K_SCALAR ? 1 : kind == K_RECOLL ? 2 : 3; }
+// Group of the queue order an instance belongs to, most work per instance
+// first: gamma = 2, 3 (general kernel); gamma = 1 with the reconstructed
+// collision; gamma = 1 with the leaves collision (fast kernel, or the scalar
+// kernel when every instance of the group has one field).
+constexpr int NGROUP = 3;
+int group_of(const InstDesc &h) { return h.gamma > 1 ? 0 : h.collision != 0 ? 1 : 2; }
 
 thread_local std::string g_create_error;
 
@@ -108,11 +105,13 @@ struct mr_ctx {
     int grid[NKIND] = {};      // blocks per launch, by kernel variant (K_*)
     int mask_cap[NKIND] = {};  // words per bitmask a block team keeps in shared memory, by variant
     int wmax = 0;              // mask words of the largest instance
-    int n_group[NKIND] = {};   // instances per group of the queue order (kGroupKind)
+    int n_group[3] = {};       // instances per group of the queue order (group_of)
+    int group_kind[3] = {K_GENERAL, K_RECOLL, K_FAST};  // kernel variant of each group
     // The groups run as separate kernels; a second stream lets one group's
     // kernel fill the SMs that another's tail leaves idle (fork and join by events).
     cudaStream_t side = nullptr;
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    int prio_least = 0, prio_greatest = 0;  // the device's launch priority range
     bool order_by_fields = true;
     std::vector<int> order_host;  // staging of the queue order (kept alive for the async copy)
     long long launches = 0;
@@ -225,7 +224,7 @@ static void layout(mr_ctx *c) {
         size_t oV = 0, oPhi = align_up(oV + vb * q * S), oM = align_up(oPhi + vb * q * (N + 1));
         size_t oL = align_up(oM + sizeof(uint32_t) * NMASK * W);
         // every list holds distinct cells of the instance, so S entries always suffice
-        long long caps[NLIST] = {S, S, S, S, S};
+        long long caps[NLIST] = {S, S, S, S};
         long long lo = 0;
         for (int L = 0; L < NLIST; ++L) {
             h.list_off[L] = lo;
@@ -310,7 +309,7 @@ static void make_tables(Tables<double> &td, Tables<float> &tf) {
 }
 
 static int launch_group(mr_ctx *c, int phases, int nsteps, const int *order, int n, int kind, const void *aux0,
-                        const void *aux1, cudaStream_t stream) {
+                        const void *aux1, cudaStream_t stream, int priority) {
     LaunchArgs a{};
     a.descs = (const InstDesc *)(c->ws + c->off_desc);
     a.order = order;
@@ -326,29 +325,33 @@ static int launch_group(mr_ctx *c, int phases, int nsteps, const int *order, int
     int rc = c->cuda(cudaMemsetAsync(a.queue, 0, sizeof(int), stream), "cudaMemsetAsync");
     if (rc) return rc;
     int grid = std::min(a.n, c->grid[kind]);
-    int e = mrg_launch(c->fp32(), c->block, std::max(grid, 1), a, stream);
+    int e = mrg_launch(c->fp32(), c->block, std::max(grid, 1), a, stream, priority);
     ++c->launches;
     if (e) return c->cuda((cudaError_t)e, "kernel launch");
     return MR_OK;
 }
 
-// A launch over the instances.  The queue order holds up to four groups, each
-// run by its own kernel variant: the fast kernel (gamma = 1, leaves collision,
-// two or more fields), the scalar kernel (the same for one field), the
-// reconstructed-collision kernel (gamma = 1) and the general kernel (gamma =
-// 2, 3).  With more than one group the groups alternate between the context's
-// stream and a side stream that forks from it and joins it again, so the
-// launches overlap.
+// A launch over the instances.  The queue order holds up to three groups, each
+// run by its own kernel variant: the general kernel (gamma = 2, 3), the
+// reconstructed-collision kernel (gamma = 1) and the fast kernel (gamma = 1,
+// leaves collision; the scalar kernel when all of them have one field).  With
+// more than one group the groups alternate between the context's stream and a
+// side stream that forks from it and joins it again, so a group's kernel can
+// fill the SMs the previous one's tail leaves idle.  Launch priorities (earlier
+// groups first, the last at the default) ask the block scheduler to place the
+// group with the most work per instance first when both kernels wait for SMs;
+// a kernel that reached the SMs first keeps them until its queue runs dry.
 static int launch(mr_ctx *c, int phases, int nsteps, int only_inst, const void *aux0, const void *aux1) {
     if (!c->bound) return c->fail(MR_ERR_STATE, "context not bound to a workspace");
     if (only_inst >= 0) {
-        const int kind = kind_of(c->hdesc[only_inst], false);
+        const InstDesc &h = c->hdesc[only_inst];
+        const int kind = h.gamma > 1 ? K_GENERAL : h.collision != 0 ? K_RECOLL : K_FAST;
         return launch_group(c, phases, nsteps, (const int *)(c->ws + c->off_ident) + only_inst, 1, kind, aux0, aux1,
-                            c->stream);
+                            c->stream, c->prio_least);
     }
     const int *order = (const int *)(c->ws + c->off_order);
     int groups = 0;
-    for (int g = 0; g < NKIND; ++g) groups += c->n_group[g] > 0;
+    for (int g = 0; g < NGROUP; ++g) groups += c->n_group[g] > 0;
     const bool fork = groups > 1;
     int rc = MR_OK;
     if (fork) {
@@ -356,11 +359,13 @@ static int launch(mr_ctx *c, int phases, int nsteps, int only_inst, const void *
         if ((rc = c->cuda(cudaStreamWaitEvent(c->side, c->ev_fork, 0), "cudaStreamWaitEvent"))) return rc;
     }
     int first = 0, k = 0;
-    for (int g = 0; g < NKIND && !rc; ++g) {
+    for (int g = 0; g < NGROUP && !rc; ++g) {
         if (c->n_group[g] == 0) continue;
-        cudaStream_t st = (fork && (k++ & 1)) ? c->side : c->stream;
-        rc = launch_group(c, phases, nsteps, order + first, c->n_group[g], kGroupKind[g], aux0, aux1, st);
+        cudaStream_t st = (fork && (k & 1)) ? c->side : c->stream;
+        const int prio = std::max(c->prio_greatest, c->prio_least - (groups - 1 - k));
+        rc = launch_group(c, phases, nsteps, order + first, c->n_group[g], c->group_kind[g], aux0, aux1, st, prio);
         first += c->n_group[g];
+        ++k;
     }
     if (fork) {
         // join even after a failed launch, so the side stream never outlives the caller's order
@@ -513,7 +518,7 @@ static int upload_order(mr_ctx *c) {
     std::vector<int> order(n);
     for (int i = 0; i < n; ++i) order[i] = i;
     std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
-        const int gx = group_of(kind_of(dd[x], true)), gy = group_of(kind_of(dd[y], true));
+        const int gx = group_of(dd[x]), gy = group_of(dd[y]);
         if (gx != gy) return gx < gy;  // kernel variant groups
         const int vx = variant_of(dd[x].eq), vy = variant_of(dd[y].eq);
         if (c->order_by_fields && vx != vy) return vx > vy;
@@ -522,8 +527,16 @@ static int upload_order(mr_ctx *c) {
         return cx > cy;
     });
     c->order_host = order;
-    for (int g = 0; g < NKIND; ++g) c->n_group[g] = 0;
-    for (int i = 0; i < n; ++i) ++c->n_group[group_of(kind_of(dd[i], true))];
+    for (int g = 0; g < NGROUP; ++g) c->n_group[g] = 0;
+    bool scalar_only = true;  // every gamma = 1 leaves-collision instance has one field
+    for (int i = 0; i < n; ++i) {
+        ++c->n_group[group_of(dd[i])];
+        if (group_of(dd[i]) == 2 && variant_of(dd[i].eq) != 1) scalar_only = false;
+    }
+    // A mixed group stays in one fast kernel: split into fast and scalar
+    // kernels on two streams it ran 2 % faster or 5 % slower than one kernel,
+    // depending on which kernel's blocks reached the SMs first.
+    c->group_kind[2] = scalar_only ? K_SCALAR : K_FAST;
     return c->cuda(cudaMemcpyAsync(c->ws + c->off_order, c->order_host.data(), sizeof(int) * n, cudaMemcpyHostToDevice,
                                    c->stream),
                    "upload");
@@ -543,7 +556,9 @@ mr_status mr_bind(mr_ctx *c, void *ws, size_t bytes, void *stream) {
     if ((rc = c->cuda(cudaGetDevice(&dev), "cudaGetDevice"))) return (mr_status)rc;
     if ((rc = c->cuda(cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, dev), "attribute"))) return (mr_status)rc;
     if (!c->side) {
-        if ((rc = c->cuda(cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking), "cudaStreamCreateWithFlags")) ||
+        if ((rc = c->cuda(cudaDeviceGetStreamPriorityRange(&c->prio_least, &c->prio_greatest),
+                          "cudaDeviceGetStreamPriorityRange")) ||
+            (rc = c->cuda(cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking), "cudaStreamCreateWithFlags")) ||
             (rc = c->cuda(cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming), "cudaEventCreateWithFlags")) ||
             (rc = c->cuda(cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming), "cudaEventCreateWithFlags")))
             return (mr_status)rc;

@@ -4,7 +4,7 @@
 #include "mr_common.h"
 
 #define MRG_DECLARE(TAG)                                        \
-    int mrg_launch_##TAG(int, const mrg::LaunchArgs &, cudaStream_t); \
+    int mrg_launch_##TAG(int, const mrg::LaunchArgs &, cudaStream_t, int); \
     int mrg_occ_##TAG(int, int, int *);                         \
     int mrg_minb_##TAG(int);                                    \
     size_t mrg_smem_##TAG(int);
@@ -36,9 +36,9 @@ MRG_DECLARE(f32_1024)
     }                                            \
     return FAIL;
 
-int mrg_launch(bool fp32, int block, int grid, const mrg::LaunchArgs &a, void *stream) {
+int mrg_launch(bool fp32, int block, int grid, const mrg::LaunchArgs &a, void *stream, int priority) {
     cudaStream_t s = (cudaStream_t)stream;
-#define MRG_CALL(TAG) mrg_launch_##TAG(grid, a, s)
+#define MRG_CALL(TAG) mrg_launch_##TAG(grid, a, s, priority)
     MRG_ROUTE(MRG_CALL, (int)cudaErrorInvalidValue)
 #undef MRG_CALL
 }

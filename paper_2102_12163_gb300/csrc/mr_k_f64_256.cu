@@ -1,4 +1,4 @@
 // double values, 256 threads per block.
 #include "mr_kernels.cuh"
 
-MRG_INSTANTIATE(double, 256, 4, 5, 3, f64_256)
+MRG_INSTANTIATE(double, 256, 4, 5, 3, 3, f64_256)

@@ -752,6 +752,38 @@ struct Worker {
         }
     }
 
+    // A1 right after a step of a D1Q2^n scheme, by conservation.  The stream
+    // (S5) moved every leaf by w (Phi[first] - Phi[next]) with w = +-2^-dj, one
+    // value of Phi per interface shared by the two cells it separates, so the
+    // size-weighted mean of the leaves under an internal cell moved by the same
+    // expression at the cell's own two edges (the inner interfaces cancel), and
+    // the internal cells still hold the projection of f* (S2; ghosts lie outside
+    // the tree).  One update of every internal cell, all levels in one pass,
+    // therefore equals the level-by-level projection of the streamed leaves up
+    // to rounding, and replaces its Jmax - Jmin dependent passes.
+    __device__ void project_by_flux() {
+        const uint32_t *li = list(L_INT);
+        const int b = sm.seg[L_INT][d.Jmin], e = sm.seg[L_INT][d.Jmax];
+        for (int i = b + tid; i < e; i += TS) {
+            const uint32_t ent = li[i];
+            const int l = ent >> KBITS;
+            const long long k = ent & KMASK;
+            const int dj = d.Jmax - l;
+            long long first = k << dj, next = (k + 1) << dj;
+            if (d.bc == 0) next &= d.N - 1;
+            const T w = (T)ldexpf(1.0f, -dj);
+#pragma unroll
+            for (int h = 0; h < QMAX; ++h)
+                if (h < q) {
+                    const T *ph = Phi + (long long)h * (d.N + 1);
+                    const T coef = (h & 1) ? -w : w;
+                    T *r = row(h, l);
+                    r[k] = r[k] + coef * (ph[first] - ph[next]);
+                }
+        }
+        sync();
+    }
+
     // ---- A2: details of the pairs of the tree, threshold T, Harten flags ----
     // FP64: the detail of Section 3.2 in double.  FP32: the detail in float with
     // a rigorous bound on its rounding error; only when a threshold lies within
@@ -762,14 +794,15 @@ struct Worker {
             details_wide();
             return;
         }
-        const uint32_t *lst = list(L_EVEN);
-        int b = sm.seg[L_EVEN][d.Jmin + 1], e = sm.seg[L_EVEN][d.Jmax + 1];
+        // the even cells of the tree above Jmin: first children 2p of the internal cells p
+        const uint32_t *lst = list(L_INT);
+        int b = sm.seg[L_INT][d.Jmin], e = sm.seg[L_INT][d.Jmax];
         uint32_t *keep = mask(M_KEEP), *ref = mask(M_REF);
         for (int i = b + tid; i < e; i += TS) {
             uint32_t ent = lst[i];
-            int l = ent >> KBITS;
+            int l = (int)(ent >> KBITS) + 1;
             const bool hasref = l < d.Jmax;
-            long long k = ent & KMASK, p = k >> 1;
+            long long p = ent & KMASK, k = 2 * p;
             long long pl = wrapc(p - 1, l - 1, d.bc), pr = wrapc(p + 1, l - 1, d.bc);
             bool keepit, refit, tie = false;
             if constexpr (sizeof(T) == 8) {
@@ -831,15 +864,15 @@ struct Worker {
     // the number of operations, (6 gamma + 2) u times the sum of |inputs|
     // (3 gamma + 1 roundings, each at most u times that sum, with a factor 2 margin)
     __device__ __noinline__ void details_wide() {
-        const uint32_t *lst = list(L_EVEN);
-        const int b = sm.seg[L_EVEN][d.Jmin + 1], e = sm.seg[L_EVEN][d.Jmax + 1], g = d.gamma;
+        const uint32_t *lst = list(L_INT);  // first children 2p of the internal cells p
+        const int b = sm.seg[L_INT][d.Jmin], e = sm.seg[L_INT][d.Jmax], g = d.gamma;
         const T *c = tab.pc[g];
         uint32_t *keep = mask(M_KEEP), *ref = mask(M_REF);
         for (int i = b + tid; i < e; i += TS) {
             const uint32_t ent = lst[i];
-            const int l = ent >> KBITS;
+            const int l = (int)(ent >> KBITS) + 1;
             const bool hasref = l < d.Jmax;
-            const long long k = ent & KMASK, p = k >> 1;
+            const long long p = ent & KMASK, k = 2 * p;
             bool keepit, refit, tie = false;
             double Dd = 0.0;
             float Df = 0.0f, B = 0.0f;
@@ -1094,7 +1127,6 @@ struct Worker {
     __device__ __forceinline__ void word_lists(const uint32_t *Rn, int g, int l, uint32_t (&m)[NLIST]) {
         uint32_t r = Rn[g], lf = mask(M_LEAF)[g];
         m[L_INT] = r & ~lf;
-        m[L_EVEN] = l > d.Jmin ? (r & 0x55555555u) : 0u;
         m[L_LEAF] = lf;
         m[L_PRED] = mask(M_PRED)[g];
         m[L_GH] = mask(M_GH)[g];
@@ -1109,12 +1141,12 @@ struct Worker {
         const int lane = tid & 31, warp = tid >> 5;
         const int Wtot = d.Wtot;
         uint32_t *pr = mask(M_PRED), *gh = mask(M_GH);
-        int run[NLIST] = {0, 0, 0, 0, 0};
+        int run[NLIST] = {0, 0, 0, 0};
         for (int r = 0, base = 0; base < Wtot; ++r, base += TS) {
             const int g = base + tid;
             const bool valid = g < Wtot;
             int l = 0, wi = 0;
-            uint32_t m[NLIST] = {0u, 0u, 0u, 0u, 0u};
+            uint32_t m[NLIST] = {0u, 0u, 0u, 0u};
             if (valid) {
                 level_of_word(sm, g, l, wi);
                 word_lists(Rn, g, l, m);
@@ -1199,7 +1231,10 @@ struct Worker {
     __device__ void adapt() {
         uint32_t *Ro = mask(sm.cur), *Rn = mask(sm.cur ^ 1);
         tick(NPHASE);
-        upsweep();
+        if (!DQ && (sm.status & ST_FLUXED))
+            project_by_flux();
+        else
+            upsweep();
         sync();
         tick(T_UPSWEEP_A);
         details();
@@ -1217,6 +1252,7 @@ struct Worker {
         if (tid == 0) {
             sm.cur ^= 1;
             sm.updates += (unsigned long long)sm.nleaf;
+            sm.status &= ~(int)ST_FLUXED;  // new tree: its internal cells are projections of f
         }
         sync();
     }
@@ -1626,6 +1662,7 @@ struct Worker {
                 sm.mass[j] = macc[j];
             }
             sm.steps += 1ULL;
+            sm.status |= ST_FLUXED;  // before the barrier: every thread of the next A1 sees it
         }
         sync();
     }
@@ -1715,6 +1752,7 @@ struct Worker {
     // ---- multiresolution reconstruction on the finest level (measurement) ----
     __device__ __noinline__ void finest(double *out) {
         upsweep();
+        if (tid == 0) sm.status &= ~(int)ST_FLUXED;  // internal cells now project f, not f*
         sync();
         const uint32_t *R = mask(sm.cur);
         for (int l = d.Jmin + 1; l <= d.Jmax; ++l) {
@@ -1905,11 +1943,11 @@ __global__ void __launch_bounds__(NT, MINB) mr_persistent(LaunchArgs a) {
 
 // One translation unit per (precision, block size) instantiation keeps the
 // build parallel; mr_dispatch.cu routes a launch to the right one.  MINB,
-// MINB_S and MINB_G are the resident blocks per SM the fast, scalar and
-// general kernels are compiled for (K_RECOLL takes MINB): the scalar code fits
-// in fewer registers, the wide-stencil code runs faster with more registers and
-// fewer resident blocks.
-#define MRG_INSTANTIATE(T, NT, MINB, MINB_S, MINB_G, TAG)                                          \
+// MINB_S, MINB_G and MINB_R are the resident blocks per SM the fast, scalar,
+// general and reconstructed-collision kernels are compiled for: the scalar
+// code fits in fewer registers, the wide-stencil code runs faster with more
+// registers and fewer resident blocks.
+#define MRG_INSTANTIATE(T, NT, MINB, MINB_S, MINB_G, MINB_R, TAG)                                  \
     static size_t mrg_dyn_##TAG(int mask_words) {                                                 \
         size_t base = (sizeof(mrg::BlockSmem<T, NT>) + 15) / 16 * 16;                              \
         return base + (size_t)mask_words * mrg::NMASK * sizeof(uint32_t);                          \
@@ -1921,25 +1959,38 @@ __global__ void __launch_bounds__(NT, MINB) mr_persistent(LaunchArgs a) {
     }                                                                                             \
     static int mrg_attr_##TAG() {                                                                 \
         static int rc = mrg_allow_##TAG<MINB, mrg::K_FAST>() | mrg_allow_##TAG<MINB_G, mrg::K_GENERAL>() | \
-                        mrg_allow_##TAG<MINB_S, mrg::K_SCALAR>() | mrg_allow_##TAG<MINB, mrg::K_RECOLL>(); \
+                        mrg_allow_##TAG<MINB_S, mrg::K_SCALAR>() | mrg_allow_##TAG<MINB_R, mrg::K_RECOLL>(); \
         return rc;                                                                                \
     }                                                                                             \
     template <int M, int K>                                                                       \
     static int mrg_occ1_##TAG(size_t dyn, int *nb) {                                              \
         return (int)cudaOccupancyMaxActiveBlocksPerMultiprocessor(nb, mrg::mr_persistent<T, NT, M, K>, NT, dyn); \
     }                                                                                             \
-    int mrg_launch_##TAG(int grid, const mrg::LaunchArgs &a, cudaStream_t s) {                     \
+    template <int M, int K>                                                                       \
+    static int mrg_go_##TAG(int grid, const mrg::LaunchArgs &a, size_t dyn, cudaStream_t s, int prio) { \
+        cudaLaunchConfig_t cfg = {};                                                              \
+        cfg.gridDim = dim3((unsigned)grid);                                                       \
+        cfg.blockDim = dim3(NT);                                                                  \
+        cfg.dynamicSmemBytes = dyn;                                                               \
+        cfg.stream = s;                                                                           \
+        cudaLaunchAttribute at[1];                                                                \
+        at[0].id = cudaLaunchAttributePriority;                                                   \
+        at[0].val.priority = prio;                                                                \
+        cfg.attrs = at;                                                                           \
+        cfg.numAttrs = 1;                                                                         \
+        return (int)cudaLaunchKernelEx(&cfg, mrg::mr_persistent<T, NT, M, K>, a);                 \
+    }                                                                                             \
+    int mrg_launch_##TAG(int grid, const mrg::LaunchArgs &a, cudaStream_t s, int prio) {           \
         int rc = mrg_attr_##TAG();                                                                \
         if (rc) return rc;                                                                        \
         const size_t dyn = mrg_dyn_##TAG(a.smem_mask_words);                                       \
         switch (a.kind) {                                                                         \
-        case mrg::K_FAST: mrg::mr_persistent<T, NT, MINB, mrg::K_FAST><<<grid, NT, dyn, s>>>(a); break; \
-        case mrg::K_GENERAL: mrg::mr_persistent<T, NT, MINB_G, mrg::K_GENERAL><<<grid, NT, dyn, s>>>(a); break; \
-        case mrg::K_SCALAR: mrg::mr_persistent<T, NT, MINB_S, mrg::K_SCALAR><<<grid, NT, dyn, s>>>(a); break; \
-        case mrg::K_RECOLL: mrg::mr_persistent<T, NT, MINB, mrg::K_RECOLL><<<grid, NT, dyn, s>>>(a); break; \
-        default: return (int)cudaErrorInvalidValue;                                               \
+        case mrg::K_FAST: return mrg_go_##TAG<MINB, mrg::K_FAST>(grid, a, dyn, s, prio);           \
+        case mrg::K_GENERAL: return mrg_go_##TAG<MINB_G, mrg::K_GENERAL>(grid, a, dyn, s, prio);   \
+        case mrg::K_SCALAR: return mrg_go_##TAG<MINB_S, mrg::K_SCALAR>(grid, a, dyn, s, prio);     \
+        case mrg::K_RECOLL: return mrg_go_##TAG<MINB_R, mrg::K_RECOLL>(grid, a, dyn, s, prio);     \
         }                                                                                         \
-        return (int)cudaGetLastError();                                                           \
+        return (int)cudaErrorInvalidValue;                                                        \
     }                                                                                             \
     int mrg_occ_##TAG(int kind, int mask_words, int *nb) {                                        \
         int rc = mrg_attr_##TAG();                                                                \
@@ -1949,11 +2000,12 @@ __global__ void __launch_bounds__(NT, MINB) mr_persistent(LaunchArgs a) {
         case mrg::K_FAST: return mrg_occ1_##TAG<MINB, mrg::K_FAST>(dyn, nb);                       \
         case mrg::K_GENERAL: return mrg_occ1_##TAG<MINB_G, mrg::K_GENERAL>(dyn, nb);               \
         case mrg::K_SCALAR: return mrg_occ1_##TAG<MINB_S, mrg::K_SCALAR>(dyn, nb);                 \
-        case mrg::K_RECOLL: return mrg_occ1_##TAG<MINB, mrg::K_RECOLL>(dyn, nb);                   \
+        case mrg::K_RECOLL: return mrg_occ1_##TAG<MINB_R, mrg::K_RECOLL>(dyn, nb);                   \
         }                                                                                         \
         return (int)cudaErrorInvalidValue;                                                        \
     }                                                                                             \
     int mrg_minb_##TAG(int kind) {                                                                \
-        return kind == mrg::K_SCALAR ? MINB_S : kind == mrg::K_GENERAL ? MINB_G : MINB;            \
+        return kind == mrg::K_SCALAR ? MINB_S : kind == mrg::K_GENERAL ? MINB_G                     \
+             : kind == mrg::K_RECOLL ? MINB_R : MINB;                                             \
     }                                                                                             \
     size_t mrg_smem_##TAG(int mask_words) { return mrg_dyn_##TAG(mask_words); }

@@ -183,7 +183,7 @@ extern "C" mr_status mr_run_static(const mr_instance_desc *desc, int precision, 
         a.aux0 = i == 0 ? (const void *)m_cons : i == 2 ? (const void *)m_finest : nullptr;
         if ((e = cudaMemsetAsync(a.queue, 0, sizeof(int), s)) != cudaSuccess)
             return fail(MR_ERR_CUDA, "mr_run_static: queue reset failed (%lld)", (long long)e);
-        int rc = mrg_launch(fp32, block, 1, a, s);
+        int rc = mrg_launch(fp32, block, 1, a, s, 0);
         if (rc) return fail(MR_ERR_CUDA, "mr_run_static: kernel launch failed (%lld)", (long long)rc);
     }
     if (updates) {
