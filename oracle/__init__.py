@@ -6,11 +6,12 @@ does.  The C source (``mrlbm_oracle.c``) follows the paper's definitions with
 dense per-level arrays; this module only compiles it and marshals numpy arrays.
 
 Parity status: every operator is pinned by a test against a fact the paper or
-the mathematics fixes (see ``tests/test_oracle_*.py``), except the vectorial
-D1Q2^2 shallow-water equilibrium, which the paper does not print (it is built
-by analogy with the vectorial Euler scheme of Section 5.3 and the flux of the
-shallow water system of Section 5.2): parity unpinned for that equilibrium
-beyond the scheme-independent invariants.
+the mathematics fixes (see ``tests/test_oracle_*.py``).  The vectorial D1Q2^2
+shallow-water equilibrium is not printed in the paper (it is built by analogy
+with the vectorial Euler scheme of Section 5.3 and the flux of the shallow
+water system of Section 5.2); it is pinned by the closed-form flux and by the
+convergence of its uniform scheme to the exact entropy solution of the dam
+break, not by a value the paper gives.
 """
 from __future__ import annotations
 

@@ -288,3 +288,25 @@ def test_adaptive_advection_at_lattice_speed_tracks_the_exact_shift():
             o.step()
             err = inst.dx * np.abs(o.finest_moments()[0] - np.roll(inst.m0[0], n)).sum()
             assert err <= 4.0 * eps * (n + 1)
+
+
+def test_vectorial_shallow_water_converges_to_the_exact_dam_break():
+    """Pin of the vectorial D1Q2^2 shallow-water equilibrium (m^1eq = m^2,
+    m^3eq = (m^2)^2 / m^0 + g (m^0)^2 / 2; a scheme the paper does not print):
+    the uniform reference scheme converges to the exact entropy solution of the
+    dam break (rarefaction to the left, shock to the right, both exact from the
+    Riemann invariants and the Rankine-Hugoniot relation) as the lattice is
+    refined.  A dropped g h^2 / 2, a wrong sign or swapped moments would
+    converge to another solution, and the error would stop shrinking."""
+    Es = []
+    for J in (8, 9, 10):
+        inst = W.shallow_water(Jmax=J, T=0.2)
+        p = params_of(inst)
+        F = O.equilibrium(p, inst.m0)
+        nsteps = int(round(0.2 / (inst.dx / inst.lam)))
+        for _ in range(nsteps):
+            F = O.uniform_step(p, F)
+        ex = W.sw_riemann_exact(W.cell_edges(inst.a, inst.b, J), nsteps * inst.dx / inst.lam)
+        Es.append(inst.dx * np.abs(O.moments(p, F) - ex).sum())
+    assert Es[1] < 0.85 * Es[0] and Es[2] < 0.85 * Es[1], Es
+    assert Es[2] < 0.05, Es
