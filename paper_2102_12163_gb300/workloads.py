@@ -301,6 +301,78 @@ def sw_riemann_exact(edges: np.ndarray, t: float, hl: float = 2.0, hr: float = 1
     return np.stack([h.mean(axis=1), (h * u).mean(axis=1)]).reshape(2, n)
 
 
+def euler_riemann_exact(edges: np.ndarray, t: float, left=(1.0, 0.0, 1.0), right=(0.125, 0.0, 0.1),
+                        gas: float = GAMMA_GAS, sub: int = 64) -> np.ndarray:
+    """Cell averages of (rho, rho u, E) of the exact solution of the Euler
+    Riemann problem with primitive states (rho, u, p) left and right of x = 0
+    (defaults: the Sod tube), midpoint sums over `sub` points per cell.  The
+    star pressure is the root of f_L(p) + f_R(p) + u_R - u_L, each f_K the
+    shock (Rankine-Hugoniot) or rarefaction (Riemann invariant) branch, found by
+    bisection; the solution is then sampled on x / t."""
+    rl, ul, pl = left
+    rr, ur, pr = right
+    al, ar = math.sqrt(gas * pl / rl), math.sqrt(gas * pr / rr)
+
+    def f(p, r, pk, ak):
+        if p > pk:  # shock
+            A, B = 2.0 / ((gas + 1.0) * r), (gas - 1.0) / (gas + 1.0) * pk
+            return (p - pk) * math.sqrt(A / (p + B))
+        return 2.0 * ak / (gas - 1.0) * ((p / pk) ** ((gas - 1.0) / (2.0 * gas)) - 1.0)
+
+    lo, hi = 1e-12, 10.0 * max(pl, pr)
+    for _ in range(200):  # f_L + f_R increasing in p
+        mid = 0.5 * (lo + hi)
+        if f(mid, rl, pl, al) + f(mid, rr, pr, ar) + (ur - ul) < 0.0:
+            lo = mid
+        else:
+            hi = mid
+    ps = 0.5 * (lo + hi)
+    us = 0.5 * (ul + ur) + 0.5 * (f(ps, rr, pr, ar) - f(ps, rl, pl, al))
+    gm = (gas - 1.0) / (gas + 1.0)
+
+    def sample(xi):
+        if xi < us:  # left of the contact
+            if ps > pl:  # left shock
+                rs = rl * (ps / pl + gm) / (gm * ps / pl + 1.0)
+                S = ul - al * math.sqrt((gas + 1.0) / (2.0 * gas) * ps / pl + (gas - 1.0) / (2.0 * gas))
+                return (rl, ul, pl) if xi < S else (rs, us, ps)
+            rs = rl * (ps / pl) ** (1.0 / gas)
+            head, tail = ul - al, us - al * (ps / pl) ** ((gas - 1.0) / (2.0 * gas))
+            if xi < head:
+                return rl, ul, pl
+            if xi > tail:
+                return rs, us, ps
+            u = 2.0 / (gas + 1.0) * (al + 0.5 * (gas - 1.0) * ul + xi)
+            c = 2.0 / (gas + 1.0) * (al + 0.5 * (gas - 1.0) * (ul - xi))
+            r = rl * (c / al) ** (2.0 / (gas - 1.0))
+            return r, u, pl * (c / al) ** (2.0 * gas / (gas - 1.0))
+        if ps > pr:  # right shock
+            rs = rr * (ps / pr + gm) / (gm * ps / pr + 1.0)
+            S = ur + ar * math.sqrt((gas + 1.0) / (2.0 * gas) * ps / pr + (gas - 1.0) / (2.0 * gas))
+            return (rs, us, ps) if xi < S else (rr, ur, pr)
+        rs = rr * (ps / pr) ** (1.0 / gas)
+        head, tail = ur + ar, us + ar * (ps / pr) ** ((gas - 1.0) / (2.0 * gas))
+        if xi > head:
+            return rr, ur, pr
+        if xi < tail:
+            return rs, us, ps
+        u = 2.0 / (gas + 1.0) * (-ar + 0.5 * (gas - 1.0) * ur + xi)
+        c = 2.0 / (gas + 1.0) * (ar - 0.5 * (gas - 1.0) * (ur - xi))
+        r = rr * (c / ar) ** (2.0 / (gas - 1.0))
+        return r, u, pr * (c / ar) ** (2.0 * gas / (gas - 1.0))
+
+    x = np.asarray(edges, dtype=np.float64)
+    n = x.size - 1
+    out = np.zeros((3, n))
+    for i in range(n):
+        acc = np.zeros(3)
+        for j in range(sub):
+            r, u, p = sample((x[i] + (j + 0.5) / sub * (x[i + 1] - x[i])) / t)
+            acc += (r, r * u, p / (gas - 1.0) + 0.5 * r * u * u)
+        out[:, i] = acc / sub
+    return out
+
+
 # the scalar test cases of Table 1 (Section 5.1) ------------------------------
 
 def _logcosh(y):

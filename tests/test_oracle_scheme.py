@@ -310,3 +310,42 @@ def test_vectorial_shallow_water_converges_to_the_exact_dam_break():
         Es.append(inst.dx * np.abs(O.moments(p, F) - ex).sum())
     assert Es[1] < 0.85 * Es[0] and Es[2] < 0.85 * Es[1], Es
     assert Es[2] < 0.05, Es
+
+
+def test_exact_sod_solution_balances_and_star_state():
+    """The exact Sod solution used as a pin: mass and energy conserved inside
+    [-1, 1] before the waves reach the ends, momentum grown by the pressure
+    difference (p_L - p_R) t, and star-region velocity and densities equal on
+    both sides of the contact where the pressure and velocity must agree."""
+    e = W.cell_edges(-1.0, 1.0, 7)
+    dx = 2.0 / 128
+    for t in (0.1, 0.2):
+        ex = W.euler_riemann_exact(e, t, sub=16)
+        assert abs(ex[0].sum() * dx - 1.125) < 1e-3
+        assert abs(ex[2].sum() * dx - 2.75) < 1e-3
+        assert abs(ex[1].sum() * dx - 0.9 * t) < 1e-3
+    # two points in the star region, left and right of the contact
+    l, r = (W.euler_riemann_exact(np.array([x, x + 1e-9]), 1.0, sub=1)[:, 0] for x in (0.5, 1.2))
+    ul, ur = l[1] / l[0], r[1] / r[0]
+    pl_, pr_ = [(W.GAMMA_GAS - 1.0) * (s[2] - 0.5 * s[1] ** 2 / s[0]) for s in (l, r)]
+    assert abs(ul - ur) < 1e-9 and abs(pl_ - pr_) < 1e-9
+    assert l[0] > r[0]  # the contact separates the denser expanded gas from the shocked gas
+
+
+def test_vectorial_euler_converges_to_the_exact_sod_tube():
+    """Pin of the vectorial D1Q2^3 Euler scheme of Section 5.3 beyond its
+    closed-form flux: the uniform reference scheme converges to the exact Sod
+    solution (rarefaction, contact, shock) as the lattice is refined; an error
+    in the equilibrium would converge to something else."""
+    Es = []
+    for J in (8, 9, 10):
+        inst = W.sod(Jmax=J, T=0.2)
+        p = params_of(inst)
+        F = O.equilibrium(p, inst.m0)
+        nsteps = int(round(0.2 / (inst.dx / inst.lam)))
+        for _ in range(nsteps):
+            F = O.uniform_step(p, F)
+        ex = W.euler_riemann_exact(W.cell_edges(inst.a, inst.b, J), nsteps * inst.dx / inst.lam, sub=8)
+        Es.append(inst.dx * np.abs(O.moments(p, F) - ex).sum())
+    assert Es[1] < 0.85 * Es[0] and Es[2] < 0.85 * Es[1], Es
+    assert Es[2] < 0.08, Es
