@@ -6,7 +6,8 @@
 // atomic work queue sorted largest first (persistent launch).  Inside a step:
 //
 //   adapt (Section 4.1)
-//     A1  projection up the current tree (Def. Projection operator)
+//     A1  projection up the current tree (Def. Projection operator); right
+//         after a D1Q2^n step, one conservative update of the internal cells
 //     A2  details of the pairs of the tree, threshold T, Harten flags (Sections
 //         3.2, 3.4, 4.2) -> KEEP / REF bitmasks
 //     A3  enlargement H: same-level dilation and children of REF pairs
@@ -20,7 +21,7 @@
 //     S3  ghost prediction coarse to fine (reconstruction operator, Section 3.3)
 //     S4  boundary reconstruction on the first / last finest cell of every
 //         leaf from the per-level-gap tables -> interface array Phi
-//     S5  compact stream (eq. AdaptiveStreamPhase) + FP64 mass audit
+//     S5  compact stream (eq. AdaptiveStreamPhase) + mass audit (FP64 totals)
 //
 // The cell arrays are dense per level (every cell of every level has a slot),
 // the tree is a set of bitmasks with 32 cells per word, and every per-cell
