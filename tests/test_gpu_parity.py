@@ -387,6 +387,29 @@ def test_graph_replay_of_every_kernel_variant_equals_advance():
         assert a.stats() == b.stats()
 
 
+def test_queue_order_and_autotune_leave_results_unchanged_on_every_variant():
+    """On a batch that needs three kernel variants (forked launches), the
+    results do not depend on the queue order (by scheme or by size) nor on an
+    autotuning pass (its trials run on a saved copy of the state)."""
+    insts = _mixed_kinds_batch()
+    for prec in (MR_FP64, MR_FP32_MIXED):
+        a, b, c = (_solver(insts, precision=prec) for _ in range(3))
+        b.set_order(False)
+        a.advance(2)
+        b.advance(2)
+        c.advance(2)
+        tune = c.autotune(2)
+        assert tune["block"] in (128, 256, 512, 1024) and tune["order_by_fields"]
+        for s in (a, b, c):
+            s.advance(6)
+            s.sync()
+        for i in range(len(insts)):
+            for s in (b, c):
+                assert np.array_equal(a.tree(i), s.tree(i)), (prec, i)
+                assert np.array_equal(a.leaves(i)[2], s.leaves(i)[2]), (prec, i)
+        assert a.stats() == b.stats() == c.stats()
+
+
 @pytest.mark.parametrize("test", ["I", "II", "III", "IV"])
 def test_scalar_tests_full_run_errors(test):
     """Tests I-IV of Table 1 run to their final time on the GPU: the FP64 path's
