@@ -216,6 +216,7 @@ static void layout(mr_ctx *c) {
         h.lam = d.lambda;
         h.eqp = d.eq_param;
         for (int j = 0; j < 3; ++j) h.s[j] = d.s[j];
+        fill_float_constants(h);
         h.S = S;
         h.N = N;
         h.m_off = c->m_off[i];

@@ -233,6 +233,25 @@ __device__ __forceinline__ T half_of(T x) {
         return T(0.5) * x;
 }
 
+// the scheme constants in the path's precision: FP64, or the float copies the
+// host rounds once (no double-to-float conversion per cell in the FP32 path)
+template <typename T>
+__device__ __forceinline__ T lam_of(const InstDesc &d) {
+    if constexpr (sizeof(T) == 8) return d.lam; else return d.lam_f;
+}
+template <typename T>
+__device__ __forceinline__ T eqp_of(const InstDesc &d) {
+    if constexpr (sizeof(T) == 8) return d.eqp; else return d.eqp_f;
+}
+template <typename T>
+__device__ __forceinline__ T s_of(const InstDesc &d, int i) {
+    if constexpr (sizeof(T) == 8) return d.s[i]; else return d.s_f[i];
+}
+template <typename T>
+__device__ __forceinline__ T minv_of(const InstDesc &d, int h, int i) {
+    if constexpr (sizeof(T) == 8) return d.minv[h][i]; else return d.minv_f[h][i];
+}
+
 template <typename T, int NF>
 __device__ __forceinline__ void equilibria(int eq, T eqp, const T *mc, T *meq) {
     using A = Ar<T>;
@@ -261,16 +280,16 @@ template <typename T, int NF>
 __device__ __forceinline__ void collide(const InstDesc &d, T *f) {
     using A = Ar<T>;
     T mc[NF], mn[NF], meq[NF];
-    const T lam = (T)d.lam;
+    const T lam = lam_of<T>(d);
 #pragma unroll
     for (int i = 0; i < NF; ++i) {
         mc[i] = A::add(f[2 * i], f[2 * i + 1]);
         mn[i] = A::mul(lam, A::sub(f[2 * i], f[2 * i + 1]));
     }
-    equilibria<T, NF>(d.eq, (T)d.eqp, mc, meq);
+    equilibria<T, NF>(d.eq, eqp_of<T>(d), mc, meq);
 #pragma unroll
     for (int i = 0; i < NF; ++i) {
-        T s = (T)d.s[i];
+        T s = s_of<T>(d, i);
         T mstar = A::add(A::mul(A::sub(T(1), s), mn[i]), A::mul(s, meq[i]));
         // m*/lambda: an exact power-of-two scaling when lambda = 2^k (same value as the division)
         T g = d.lam_log2 != NOT_POW2 ? scale2(mstar, -d.lam_log2) : A::div(mstar, lam);
@@ -302,7 +321,7 @@ __device__ __forceinline__ int dq_w(int h) { return h == 0 ? 0 : (h & 1) ? (h + 
 // m^{2,eq}; f* = f + M^{-1} (m* - m) (the conserved rows of m* - m are zero)
 template <typename T, int Q>
 __device__ __forceinline__ void dq_collide(const InstDesc &d, T *f) {
-    const T lam = (T)d.lam;
+    const T lam = lam_of<T>(d);
     T m[Q];
 #pragma unroll
     for (int i = 0; i < Q; ++i) m[i] = T(0);
@@ -317,19 +336,19 @@ __device__ __forceinline__ void dq_collide(const InstDesc &d, T *f) {
         }
     }
     T meq[Q];
-    meq[2] = (m[1] * m[1]) / m[0] + (T(0.5) * (T)d.eqp) * (m[0] * m[0]);
+    meq[2] = (m[1] * m[1]) / m[0] + (T(0.5) * eqp_of<T>(d)) * (m[0] * m[0]);
     if constexpr (Q == 5) {
         meq[3] = (lam * lam) * m[1];
         meq[4] = (lam * lam) * meq[2];
     }
     T dm[Q];
 #pragma unroll
-    for (int i = 2; i < Q; ++i) dm[i] = (T)d.s[i - 2] * (meq[i] - m[i]);
+    for (int i = 2; i < Q; ++i) dm[i] = s_of<T>(d, i - 2) * (meq[i] - m[i]);
 #pragma unroll
     for (int h = 0; h < Q; ++h) {
         T acc = T(0);
 #pragma unroll
-        for (int i = 2; i < Q; ++i) acc = acc + (T)d.minv[h][i] * dm[i];
+        for (int i = 2; i < Q; ++i) acc = acc + minv_of<T>(d, h, i) * dm[i];
         f[h] = f[h] + acc;
     }
 }
@@ -577,8 +596,11 @@ struct Worker {
                         lo[j] = l;
                     }
         }
+        // only thread 0 holds the sums: the other threads keep off the FP64 pipe
+        if (tid == 0)
 #pragma unroll
-        for (int j = 0; j < 3; ++j) out[j] = (double)hi[j] + (double)lo[j];
+            for (int j = 0; j < 3; ++j)
+                if (j < nf) out[j] = (double)hi[j] + (double)lo[j];
     }
 
     // ---- projection of the internal cells of level l (Def. Projection operator)
@@ -617,14 +639,14 @@ struct Worker {
     // equilibria of the relaxed moments at one cell (populations g)
     __device__ __forceinline__ void relaxed_equilibria(const T *g, T *meq) const {
         if constexpr (DQ) {
-            const T lam = (T)d.lam;
+            const T lam = lam_of<T>(d);
             T h = T(0), hu = T(0);
 #pragma unroll
             for (int c = 0; c < q; ++c) {
                 h = h + g[c];
                 hu = hu + ((T)dq_w(c) * lam) * g[c];
             }
-            meq[0] = (hu * hu) / h + (T(0.5) * (T)d.eqp) * (h * h);
+            meq[0] = (hu * hu) / h + (T(0.5) * eqp_of<T>(d)) * (h * h);
             if constexpr (q == 5) {
                 meq[1] = (lam * lam) * hu;
                 meq[2] = (lam * lam) * meq[0];
@@ -634,7 +656,7 @@ struct Worker {
             T mc[NF];
 #pragma unroll
             for (int i = 0; i < NF; ++i) mc[i] = A::add(g[2 * i], g[2 * i + 1]);
-            equilibria<T, NF>(d.eq, (T)d.eqp, mc, meq);
+            equilibria<T, NF>(d.eq, eqp_of<T>(d), mc, meq);
         }
     }
 
@@ -699,7 +721,7 @@ struct Worker {
 #pragma unroll
             for (int r = 0; r < NR; ++r) mavg[r] = Phi[r * stride + i];
             if constexpr (DQ) {
-                const T lam = (T)d.lam;
+                const T lam = lam_of<T>(d);
                 T m[q];
 #pragma unroll
                 for (int r = 0; r < q; ++r) m[r] = T(0);
@@ -715,21 +737,21 @@ struct Worker {
                 }
                 T dm[q];
 #pragma unroll
-                for (int r = 2; r < q; ++r) dm[r] = (T)d.s[r - 2] * (mavg[r - 2] - m[r]);
+                for (int r = 2; r < q; ++r) dm[r] = s_of<T>(d, r - 2) * (mavg[r - 2] - m[r]);
 #pragma unroll
                 for (int h = 0; h < q; ++h) {
                     T a = T(0);
 #pragma unroll
-                    for (int r = 2; r < q; ++r) a = a + (T)d.minv[h][r] * dm[r];
+                    for (int r = 2; r < q; ++r) a = a + minv_of<T>(d, h, r) * dm[r];
                     f[h] = f[h] + a;
                 }
             } else {
                 using A = Ar<T>;
-                const T lam = (T)d.lam;
+                const T lam = lam_of<T>(d);
 #pragma unroll
                 for (int j = 0; j < NF; ++j) {
                     const T mc = A::add(f[2 * j], f[2 * j + 1]), mn = A::mul(lam, A::sub(f[2 * j], f[2 * j + 1]));
-                    const T sj = (T)d.s[j];
+                    const T sj = s_of<T>(d, j);
                     const T mstar = A::add(A::mul(A::sub(T(1), sj), mn), A::mul(sj, mavg[j]));
                     const T g = d.lam_log2 != NOT_POW2 ? scale2(mstar, -d.lam_log2) : A::div(mstar, lam);
                     f[2 * j] = half_of<T>(A::add(mc, g));

@@ -133,6 +133,7 @@ extern "C" mr_status mr_run_static(const mr_instance_desc *desc, int precision, 
     h.lam = d.lambda;
     h.eqp = d.eq_param;
     for (int j = 0; j < 3; ++j) h.s[j] = d.s[j];
+    fill_float_constants(h);
     h.S = S;
     h.N = N;
     h.m_off = 0;
