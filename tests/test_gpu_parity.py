@@ -303,6 +303,31 @@ def test_full_size_sod_lockstep_samples():
     assert_same_leaves(lvs, o)
 
 
+def test_deepest_tree_lockstep():
+    """Jmax = 24, the deepest tree the library takes (2^24 finest cells; the
+    bitmasks no longer fit in shared memory and live in global memory): steps
+    in lock-step with the oracle give the same tree and leaves; the FP32 path
+    stays within 1e-4 (L1 of the finest moments) of the oracle."""
+    inst = W.advection(Jmax=24)
+    s = _solver(inst)
+    o = O.Oracle(params_of(inst))
+    for n in range(2):
+        R, vals, _ = gpu_state(s)
+        o.set_state(R, vals)
+        o.step()
+        s.advance(1)
+        R2, _, lvs = gpu_state(s)
+        assert np.array_equal(R2, o.get_state()[0]), n
+        assert_same_leaves(lvs, o)
+    s32 = _solver(inst, precision=MR_FP32_MIXED)
+    o2 = O.Oracle(params_of(inst))
+    o2.set_initial(inst.m0)
+    s32.advance(2)
+    o2.step(2)
+    err = inst.dx * np.abs(s32.finest() - o2.finest_moments()).sum(axis=1)
+    assert np.all(err < 1e-4), err
+
+
 def test_fp32_path_tracks_the_fp64_oracle():
     inst = W.random_smooth(11, W.EQ_EULER, seed=50, eps=1e-4, bc=W.BC_COPY)
     s = _solver(inst, precision=MR_FP32_MIXED)
