@@ -177,6 +177,7 @@ struct TeamSmem {
     double audit;
     unsigned long long updates, steps;
     int cur, nleaf, status, near_ties;
+    uint32_t deplev[2];  // levels holding transfer (0) / ghost (1) cells that wait on the same list
     int idx;
     int g0s, gbase;  // level_of_word constants
 #ifdef MRG_PHASE_TIMERS
@@ -1163,8 +1164,8 @@ struct Worker {
         constexpr int NW = TS / 32;
         const int lane = tid & 31, warp = tid >> 5;
         const int Wtot = d.Wtot;
-        uint32_t *pr = mask(M_PRED), *gh = mask(M_GH);
         int run[NLIST] = {0, 0, 0, 0};
+        if (tid == 0) sm.deplev[0] = sm.deplev[1] = 0u;  // new lists: gathered again by predict_fill
         for (int r = 0, base = 0; base < Wtot; ++r, base += TS) {
             const int g = base + tid;
             const bool valid = g < Wtot;
@@ -1173,9 +1174,6 @@ struct Worker {
             if (valid) {
                 level_of_word(sm, g, l, wi);
                 word_lists(Rn, g, l, m);
-                // consumed: as KEEP / REF these words must start the next step at zero
-                pr[g] = 0u;
-                gh[g] = 0u;
             }
             int inc[NLIST];
 #pragma unroll
@@ -1220,10 +1218,10 @@ struct Worker {
     }
 
     // ---- A6 / S3: prediction of listed cells, coarse to fine -----------------
-    __device__ __forceinline__ void predict_level(const uint32_t *lst, int L, int l) {
-        int b = sm.seg[L][l], e = sm.seg[L][l + 1];
-        for (int i = b + tid; i < e; i += TS) {
-            long long k = lst[i] & KMASK;
+    // predicts the listed cell ent (level l) from level l - 1
+    __device__ __forceinline__ void predict_entry(uint32_t ent, int l) {
+        {
+            const long long k = ent & KMASK;
             T v[QMAX];
             if constexpr (!WIDE) {
 #pragma unroll
@@ -1241,11 +1239,47 @@ struct Worker {
         }
     }
 
+    // whether the prediction stencil of cell (l, k) at level l - 1 (parent +-
+    // gamma, wrapped or clamped as the prediction does) holds a cell marked in P
+    __device__ __forceinline__ bool stencil_marked(const uint32_t *P, int l, long long k) const {
+        const int gg = WIDE ? d.gamma : 1, lp = l - 1;
+        const uint32_t *pl = P + sm.woff[lp];
+        const long long p = k >> 1;
+        bool hit = false;
+        for (int a = -gg; a <= gg; ++a) {
+            const long long c = wrapc(p + a, lp, d.bc);
+            hit |= ((pl[c >> 5] >> (c & 31)) & 1u) != 0u;
+        }
+        return hit;
+    }
+
+    // A6 / S3.  A listed cell whose stencil holds no cell of the same list reads
+    // only tree values (the old tree for the transfer, the current tree for the
+    // ghosts: the marking closes both lists under prediction stencils), so those
+    // cells go in one pass over all levels; the rest follow level by level,
+    // coarse to fine, on the levels that have any.  The marks of both lists stay
+    // in their masks until the next step's A2 clears them.
     __device__ void predict_fill(int L) {
         const uint32_t *lst = list(L);
+        const uint32_t *P = mask(L == L_GH ? M_GH : M_PRED);
+        const int slot = L == L_GH ? 1 : 0;
+        const int b = sm.seg[L][d.Jmin + 1], e = sm.seg[L][d.Jmax + 1];
+        for (int i = b + tid; i < e; i += TS) {
+            const uint32_t ent = lst[i];
+            const int l = (int)(ent >> KBITS);
+            if (stencil_marked(P, l, ent & KMASK))
+                atomicOr(&sm.deplev[slot], 1u << l);
+            else
+                predict_entry(ent, l);
+        }
+        sync();
+        const uint32_t lv = sm.deplev[slot];
         for (int l = d.Jmin + 1; l <= d.Jmax; ++l) {
-            if (sm.seg[L][l] == sm.seg[L][l + 1]) continue;
-            predict_level(lst, L, l);
+            if (!((lv >> l) & 1u)) continue;
+            for (int i = sm.seg[L][l] + tid; i < sm.seg[L][l + 1]; i += TS) {
+                const uint32_t ent = lst[i];
+                if (stencil_marked(P, l, ent & KMASK)) predict_entry(ent, l);
+            }
             sync();
         }
     }
@@ -1254,6 +1288,16 @@ struct Worker {
     __device__ void adapt() {
         uint32_t *Ro = mask(sm.cur), *Rn = mask(sm.cur ^ 1);
         tick(NPHASE);
+        {
+            // the transfer / ghost marks of the last list compaction share storage
+            // with KEEP / REF, which A2 accumulates into: clear them (the barrier of
+            // A1 orders this before A2)
+            uint32_t *pr = mask(M_PRED), *gh = mask(M_GH);
+            for (int g = tid; g < d.Wtot; g += TS) {
+                pr[g] = 0u;
+                gh[g] = 0u;
+            }
+        }
         if (!DQ && (sm.status & ST_FLUXED))
             project_by_flux();
         else
@@ -1818,6 +1862,8 @@ __device__ void load_instance(TeamSmem<T> &sm, const InstDesc &dg, int tid) {
         sm.nleaf = st.nleaf;
         sm.status = st.status;
         sm.near_ties = st.near_ties;
+        sm.deplev[0] = st.deplev[0];
+        sm.deplev[1] = st.deplev[1];
         sm.updates = st.updates;
         sm.steps = st.steps;
         sm.audit = st.audit;
@@ -1861,6 +1907,8 @@ __device__ void store_instance(TeamSmem<T> &sm, int tid) {
         st.nleaf = sm.nleaf;
         st.status = sm.status;
         st.near_ties = sm.near_ties;
+        st.deplev[0] = sm.deplev[0];
+        st.deplev[1] = sm.deplev[1];
         st.updates = sm.updates;
         st.steps = sm.steps;
         st.audit = sm.audit;
@@ -1891,8 +1939,10 @@ __device__ __forceinline__ void run_instance(TeamSmem<T> &sm, const Tables<T> &t
 }
 
 // Bitmasks live in shared memory (smask, room for `cap` words per mask) when the
-// instance fits: the current tree is copied in at the start and back at the
-// end, KEEP / REF start cleared, the other masks are rebuilt by every step.
+// instance fits: the current tree and the transfer / ghost marks (which a later
+// step's predictions read; KEEP / REF share their storage and A2 clears it) are
+// copied in at the start and back at the end; the other masks are rebuilt by
+// every step.
 template <typename T, int TS, bool WIDE, bool SCALAR>
 __device__ void run_team(TeamSmem<T> &sm, const Tables<T> &tab, BlockScratch &bx, const LaunchArgs &a,
                          const InstDesc &dg, int tid, uint32_t *smask, int cap) {
@@ -1903,10 +1953,11 @@ __device__ void run_team(TeamSmem<T> &sm, const Tables<T> &tab, BlockScratch &bx
     if (local) {
         const uint32_t *gr = sm.d.masks + (long long)sm.cur * W;
         uint32_t *lr = smask + sm.cur * W;
+        const uint32_t *gp = sm.d.masks + (long long)M_PRED * W, *gg = sm.d.masks + (long long)M_GH * W;
         for (int g = tid; g < W; g += TS) {
             lr[g] = gr[g];
-            smask[M_KEEP * W + g] = 0u;
-            smask[M_REF * W + g] = 0u;
+            smask[M_PRED * W + g] = gp[g];
+            smask[M_GH * W + g] = gg[g];
         }
         __syncthreads();
     }
@@ -1925,8 +1976,13 @@ __device__ void run_team(TeamSmem<T> &sm, const Tables<T> &tab, BlockScratch &bx
     }
     if (local) {
         uint32_t *gr = sm.d.masks + (long long)sm.cur * W;
+        uint32_t *gp = sm.d.masks + (long long)M_PRED * W, *gg = sm.d.masks + (long long)M_GH * W;
         const uint32_t *lr = smask + sm.cur * W;
-        for (int g = tid; g < W; g += TS) gr[g] = lr[g];
+        for (int g = tid; g < W; g += TS) {
+            gr[g] = lr[g];
+            gp[g] = smask[M_PRED * W + g];
+            gg[g] = smask[M_GH * W + g];
+        }
     }
     store_instance<T, TS>(sm, tid);
 }
