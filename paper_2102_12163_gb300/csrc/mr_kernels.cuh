@@ -253,6 +253,24 @@ __device__ __forceinline__ T minv_of(const InstDesc &d, int h, int i) {
     if constexpr (sizeof(T) == 8) return d.minv[h][i]; else return d.minv_f[h][i];
 }
 
+// x / lambda for a lambda that is no power of two, in FP64 bit for bit the
+// correctly rounded quotient without a division: q0 = RN(x r) with r = RN(1 / lambda) is
+// within one ulp of x / lambda, the residual x - q0 lambda is exact in one FMA,
+// and q0 + residual r rounded once is the correctly rounded quotient (P.
+// Markstein, IBM J. Res. Dev. 34(1), 1990).  Operands near the ends of the
+// exponent range, zeros and non-finite values take the division.
+template <typename T>
+__device__ __forceinline__ T div_lam(T x, const InstDesc &d) {
+    if constexpr (sizeof(T) == 8) {
+        const int e = (__double2hiint(x) >> 20) & 0x7FF;
+        if (e < 64 || e > 1983) return __ddiv_rn(x, d.lam);
+        const double q0 = __dmul_rn(x, d.rlam);
+        return __fma_rn(__fma_rn(-q0, d.lam, x), d.rlam, q0);
+    } else {
+        return __fdiv_rn(x, d.lam_f);  // FP32 divisions are cheap; the register budget is not
+    }
+}
+
 template <typename T, int NF>
 __device__ __forceinline__ void equilibria(int eq, T eqp, const T *mc, T *meq) {
     using A = Ar<T>;
@@ -293,7 +311,7 @@ __device__ __forceinline__ void collide(const InstDesc &d, T *f) {
         T s = s_of<T>(d, i);
         T mstar = A::add(A::mul(A::sub(T(1), s), mn[i]), A::mul(s, meq[i]));
         // m*/lambda: an exact power-of-two scaling when lambda = 2^k (same value as the division)
-        T g = d.lam_log2 != NOT_POW2 ? scale2(mstar, -d.lam_log2) : A::div(mstar, lam);
+        T g = d.lam_log2 != NOT_POW2 ? scale2(mstar, -d.lam_log2) : div_lam<T>(mstar, d);
         f[2 * i] = half_of<T>(A::add(mc[i], g));
         f[2 * i + 1] = half_of<T>(A::sub(mc[i], g));
     }
@@ -754,7 +772,7 @@ struct Worker {
                     const T mc = A::add(f[2 * j], f[2 * j + 1]), mn = A::mul(lam, A::sub(f[2 * j], f[2 * j + 1]));
                     const T sj = s_of<T>(d, j);
                     const T mstar = A::add(A::mul(A::sub(T(1), sj), mn), A::mul(sj, mavg[j]));
-                    const T g = d.lam_log2 != NOT_POW2 ? scale2(mstar, -d.lam_log2) : A::div(mstar, lam);
+                    const T g = d.lam_log2 != NOT_POW2 ? scale2(mstar, -d.lam_log2) : div_lam<T>(mstar, d);
                     f[2 * j] = half_of<T>(A::add(mc, g));
                     f[2 * j + 1] = half_of<T>(A::sub(mc, g));
                 }
