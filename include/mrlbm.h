@@ -31,10 +31,13 @@
  *     pointers marked "host" must be host memory.
  *   - The library is not thread-safe per context.
  *
- * Scope of this build: D = 1, vectorial D1Q2^n schemes (velocities +-lambda per
- * field), prediction stencils gamma = 1, 2, 3 (Section 3.1: c1 = -1/8; c1 =
- * -22/128, c2 = 3/128; c1 = -201/1024, c2 = 11/256, c3 = -5/1024), enlargement
- * width sigma = 1.
+ * Scope of this build: D = 1; vectorial D1Q2^n schemes, n = 1, 2, 3 (velocities
+ * +-lambda per field, Sections 5.1 and 5.3), and the D1Q3 / D1Q5 shallow water
+ * schemes (Section 5.2); prediction stencils gamma = 1, 2, 3 (Section 3.1: c1 =
+ * -1/8; c1 = -22/128, c2 = 3/128; c1 = -201/1024, c2 = 11/256, c3 = -5/1024);
+ * enlargement width sigma = max |w^h| (Section 4.2): 1 for D1Q2^n and D1Q3, 2
+ * for D1Q5; leaves collision or reconstructed collision (Section 4.5).
+ * Lattice velocities lambda in [2^-16, 2^16].
  */
 #ifndef MRLBM_H
 #define MRLBM_H
@@ -154,12 +157,20 @@ mr_status mr_sync(mr_ctx *ctx);
 
 /* ---- results (synchronising; host output pointers) -------------------- */
 
-/* Complete leaves S(Lambda) of instance inst, ordered by level then index, with
- * their q populations (f[h * cap + i]); any output may be NULL. */
+/* Complete leaves S(Lambda) of instance inst (Section 3.3: the cells of the
+ * complete tree without children, a multi-level partition of the domain),
+ * ordered by level then index, with their q populations (f[h * cap + i]); any
+ * output may be NULL.  level / index / f are host pointers of cap entries per
+ * row; *count receives #S(Lambda).  MR_ERR_CAPACITY (nothing written) when an
+ * output is given and cap < #S(Lambda); MR_ERR_NONFINITE when a population of
+ * the instance became NaN or infinite. */
 mr_status mr_get_leaves(mr_ctx *ctx, int inst, int *level, long *index, double *f, long cap,
                         long *count);
 
-/* Conserved moments on the leaves (m[j * cap + i]), same order as mr_get_leaves. */
+/* Conserved moments m^j = sum_h M_{jh} f^h on the leaves (Section 2.1, the
+ * moment matrix of the d'Humieres formalism: per D1Q2 field f+ + f-, for
+ * D1Q3 / D1Q5 the moments of order 0 and 1), host pointer m[j * cap + i],
+ * same order, count and errors as mr_get_leaves. */
 mr_status mr_get_moments(mr_ctx *ctx, int inst, double *m, long cap, long *count);
 
 /* Conserved moments reconstructed on every finest cell (n * 2^Jmax values,
@@ -170,9 +181,14 @@ mr_status mr_get_finest(mr_ctx *ctx, int inst, double *m_finest);
 /* Complete tree membership R (S bytes, cell numbering of mr_set_state). */
 mr_status mr_get_tree(mr_ctx *ctx, int inst, unsigned char *R);
 
-/* Conserved totals sum_leaves dx_l m_j (n values, returned in FP64; the FP32
- * path accumulates them in float-float, relative error near 2^-44) and the
- * largest per-step residual |mass change - boundary flux| seen so far. */
+/* Conservation audit.  The collision keeps the conserved moments of every
+ * leaf (Section 2.1) and the stream of eq. AdaptiveStreamPhase (Section 4.3)
+ * exchanges one reconstructed value per interface between the two leaves it
+ * separates, so the totals sum_leaves dx_l m^j change only by what crosses a
+ * copy boundary (periodic: not at all).  mass (host, n values) receives the
+ * totals in FP64 (the FP32 path accumulates them in float-float, relative
+ * error near 2^-44); residual (host) the largest per-step |change of the
+ * totals - boundary flux| seen so far.  Either may be NULL. */
 mr_status mr_audit(mr_ctx *ctx, int inst, double *mass, double *residual);
 
 /* Per-instance summary in one copy: FP64 conserved totals (mass[3 * i + j],
@@ -180,10 +196,37 @@ mr_status mr_audit(mr_ctx *ctx, int inst, double *mass, double *residual);
  * either output may be NULL.  Host pointers. */
 mr_status mr_get_summary(mr_ctx *ctx, double *mass, int *nleaf);
 
+/* Near ties of the threshold test (Section 3.4, Prop. ErrorControl, and the
+ * Harten rule of eq. HartenLossOfRegularity): the number of keep / refine
+ * decisions of instance inst, since its initial state, whose max |detail| lay
+ * within 1e-12 relative of eps_l or of 2^(mu_bar + 1) eps_l.  Such decisions
+ * are taken on ">=" exactly as printed, in FP64 (the FP32 path recomputes
+ * them in FP64 from the stored values); the count tells a caller comparing
+ * meshes produced elsewhere where a rounding difference could flip a cell.
+ * Host output; synchronising. */
+mr_status mr_near_ties(mr_ctx *ctx, int inst, long long *count);
+
 /* Totals over the context: leaf-cell updates (sum over steps and instances of
  * #S(Lambda^{n+1})), steps taken by instance 0, current leaves over instances. */
 mr_status mr_stats(mr_ctx *ctx, unsigned long long *updates, unsigned long long *steps,
                    long long *leaves);
+
+/* Length of the dependent-pass chain (no counterpart in the paper): the team
+ * barriers instance inst has executed since its initial state and the steps
+ * it has taken.  Every barrier ends a pass over a level or a list whose
+ * results the next pass reads, so passes / steps times the cost of one such
+ * hand-over (mr_probe_latency) is a floor under the time of one step of a
+ * lone instance.  Host outputs (either may be NULL); synchronising. */
+mr_status mr_step_passes(mr_ctx *ctx, int inst, unsigned long long *steps, unsigned long long *passes);
+
+/* Latency probe (no counterpart in the paper): one block hands a value from
+ * one warp to another through memory and a block barrier, as consecutive
+ * passes of the step do, and times it in SM clock cycles on the current
+ * device: cycles[0] per hand-over through global memory, cycles[1] through
+ * shared memory, cycles[2] per bare block barrier.  scratch: caller-owned
+ * device memory of at least 4096 bytes (256-byte aligned); synchronises the
+ * stream. */
+mr_status mr_probe_latency(void *scratch, size_t bytes, void *stream, double *cycles);
 
 /* Launch shape: threads per block (128, 256, 512 or 1024; one block advances
  * one instance at a time) and blocks (0 = one wave of resident blocks).
@@ -268,8 +311,11 @@ mr_status mr_destroy(mr_ctx *ctx);
  *             given the call waits for the stream and reports non-finite values
  *   stream    CUDA stream the work is ordered on (NULL: legacy default stream)
  * The first call on a device looks up the scratch area's device address (with
- * that device current) and keeps it; make that first call before any stream
- * capture.  An instance whose layout exceeds the area is rejected with
+ * that device current) and keeps it; that set-up is done once per device even
+ * when several host threads make their first call at the same time.  The call
+ * uploads its descriptor from host memory and may wait for the stream, so it
+ * must not be recorded into a CUDA graph: on a stream that is capturing it
+ * returns MR_ERR_STATE and enqueues nothing.  An instance whose layout exceeds the area is rejected with
  * MR_ERR_CAPACITY (FP64 Euler fits up to Jmax = 16); the message is available
  * from mr_last_error(NULL, ...).  Every call uses the same area and leaves its
  * contents behind; each call re-initialises what it reads, but calls whose

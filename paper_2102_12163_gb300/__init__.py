@@ -34,6 +34,21 @@ def _desc(inst: "workloads.Instance") -> capi.mr_instance_desc:
     return d
 
 
+def probe_latency(device: str = "cuda:0") -> dict:
+    """SM cycles of one warp-to-warp hand-over through global memory, through
+    shared memory, and of a bare block barrier (mr_probe_latency)."""
+    import torch
+
+    lib = capi.load()
+    dev = torch.device(device)
+    scratch = torch.empty(4096, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    out = (ctypes.c_double * 3)()
+    capi.check(None, lib.mr_probe_latency(ctypes.c_void_p(scratch.data_ptr()), 4096,
+                                          ctypes.c_void_p(stream.cuda_stream), out))
+    return {"global_handover_cycles": out[0], "shared_handover_cycles": out[1], "barrier_cycles": out[2]}
+
+
 class MRLBM:
     """One context of the C ABI holding one or many instances on one GPU.
 
@@ -218,6 +233,19 @@ class MRLBM:
         capi.check(self.h, self.lib.mr_get_summary(self.h, ctypes.cast(mp, ctypes.POINTER(ctypes.c_double)),
                                                    ctypes.cast(cp, ctypes.POINTER(ctypes.c_int))))
         return m, c
+
+    def near_ties(self, inst: int = 0) -> int:
+        """Threshold and Harten decisions of instance inst within 1e-12 relative
+        of their threshold since its initial state."""
+        n = ctypes.c_longlong()
+        capi.check(self.h, self.lib.mr_near_ties(self.h, inst, ctypes.byref(n)))
+        return n.value
+
+    def step_passes(self, inst: int = 0):
+        """(steps, team barriers) of instance inst since its initial state."""
+        st, ps = ctypes.c_ulonglong(), ctypes.c_ulonglong()
+        capi.check(self.h, self.lib.mr_step_passes(self.h, inst, ctypes.byref(st), ctypes.byref(ps)))
+        return st.value, ps.value
 
     def stats(self):
         u, s, lv = ctypes.c_ulonglong(), ctypes.c_ulonglong(), ctypes.c_longlong()

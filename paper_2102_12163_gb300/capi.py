@@ -51,6 +51,9 @@ SIGNATURES = {
     "mr_get_tree": [_vp, _i, _vp],
     "mr_audit": [_vp, _i, _P(_d), _P(_d)],
     "mr_get_summary": [_vp, _P(_d), _P(_i)],
+    "mr_near_ties": [_vp, _i, _P(ctypes.c_longlong)],
+    "mr_step_passes": [_vp, _i, _P(ctypes.c_ulonglong), _P(ctypes.c_ulonglong)],
+    "mr_probe_latency": [_vp, _sz, _vp, _P(_d)],
     "mr_stats": [_vp, _P(ctypes.c_ulonglong), _P(ctypes.c_ulonglong), _P(ctypes.c_longlong)],
     "mr_set_launch": [_vp, _i, _i],
     "mr_set_order": [_vp, _i],

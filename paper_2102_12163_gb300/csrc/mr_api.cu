@@ -83,6 +83,36 @@ int group_of(const InstDesc &h) { return h.gamma > 1 ? 0 : h.collision != 0 ? 1 
 
 thread_local std::string g_create_error;
 
+// Latency probe: warps 0 and 1 of one block alternately read the value the
+// other wrote and write the next one, with a block barrier after every
+// hand-over; through global memory (buf[0..63]), through shared memory, and
+// bare barriers.  Every index stays inside buf[0..63] and the shared array.
+constexpr int kProbeIters = 4096;
+__global__ void mrg_probe(int *buf, unsigned long long *res, int iters) {
+    __shared__ int sh[64];
+    if (threadIdx.x < 64) sh[threadIdx.x] = 0;
+    __syncthreads();
+    const int me = threadIdx.x;
+    long long t0 = clock64();
+    for (int i = 0; i < iters; ++i) {
+        if (me == ((i & 1) ? 32 : 0)) buf[(i + 1) & 63] = buf[i & 63] + 1;
+        __syncthreads();
+    }
+    long long t1 = clock64();
+    for (int i = 0; i < iters; ++i) {
+        if (me == ((i & 1) ? 32 : 0)) sh[(i + 1) & 63] = sh[i & 63] + 1;
+        __syncthreads();
+    }
+    long long t2 = clock64();
+    for (int i = 0; i < iters; ++i) __syncthreads();
+    long long t3 = clock64();
+    if (me == 0) {
+        res[0] = (unsigned long long)(t1 - t0);
+        res[1] = (unsigned long long)(t2 - t1) + (unsigned long long)(sh[iters & 63] & 0);
+        res[2] = (unsigned long long)(t3 - t2);
+    }
+}
+
 }  // namespace
 
 struct mr_ctx {
@@ -152,8 +182,8 @@ static int check_desc(mr_ctx *c, const mr_instance_desc &d, int i) {
         return c->fail(MR_ERR_ARG, "instance %d: collision must be 0 (leaves) or 1 (reconstructed)", i);
     if (d.bc != MR_BC_PERIODIC && d.bc != MR_BC_COPY) return c->fail(MR_ERR_ARG, "instance %d: bad boundary", i);
     if (nfields_of(d.eq) == 0) return c->fail(MR_ERR_ARG, "instance %d: bad equilibrium", i);
-    if (!(d.eps >= 0.0) || !(d.b > d.a) || !(d.lambda > 0.0))
-        return c->fail(MR_ERR_ARG, "instance %d: need eps >= 0, b > a, lambda > 0", i);
+    if (!(d.eps >= 0.0) || !(d.b > d.a) || !(d.lambda >= 0x1p-16 && d.lambda <= 0x1p16))
+        return c->fail(MR_ERR_ARG, "instance %d: need eps >= 0, b > a, 2^-16 <= lambda <= 2^16", i);
     for (int j = 0; j < nrates_of(d.eq); ++j)
         if (!(d.s[j] > 0.0 && d.s[j] <= 2.0)) return c->fail(MR_ERR_ARG, "instance %d: relaxation rate outside (0, 2]", i);
     if ((d.eq == MR_EQ_SW_D1Q3 || d.eq == MR_EQ_SW_D1Q5) && d.gamma != 1)
@@ -839,6 +869,51 @@ mr_status mr_get_summary(mr_ctx *c, double *mass, int *nleaf) {
                       "cudaMemcpy2DAsync")))
         return (mr_status)rc;
     return (mr_status)c->cuda(cudaStreamSynchronize(c->stream), "cudaStreamSynchronize");
+}
+
+mr_status mr_near_ties(mr_ctx *c, int inst, long long *count) {
+    if (!c || !count || inst < 0 || inst >= c->n()) return MR_ERR_ARG;
+    if (!c->bound) return (mr_status)c->fail(MR_ERR_STATE, "not bound");
+    InstState st;
+    int rc = read_state(c, inst, &st);
+    if (rc) return (mr_status)rc;
+    *count = st.near_ties;
+    return MR_OK;
+}
+
+mr_status mr_step_passes(mr_ctx *c, int inst, unsigned long long *steps, unsigned long long *passes) {
+    if (!c || inst < 0 || inst >= c->n()) return MR_ERR_ARG;
+    if (!c->bound) return (mr_status)c->fail(MR_ERR_STATE, "not bound");
+    InstState st;
+    int rc = read_state(c, inst, &st);
+    if (rc) return (mr_status)rc;
+    if (steps) *steps = st.steps;
+    if (passes) *passes = st.passes;
+    return MR_OK;
+}
+
+mr_status mr_probe_latency(void *scratch, size_t bytes, void *stream, double *cycles) {
+    if (!scratch || !cycles || bytes < 4096 || ((uintptr_t)scratch & 255u) != 0) {
+        mrg_set_error("mr_probe_latency: need a 256-byte aligned scratch of at least 4096 bytes and an output");
+        return MR_ERR_ARG;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    unsigned long long out[3] = {0, 0, 0};
+    int *buf = (int *)scratch;
+    unsigned long long *res = (unsigned long long *)((unsigned char *)scratch + 2048);
+    cudaError_t e = cudaMemsetAsync(scratch, 0, 4096, s);
+    if (e == cudaSuccess) {
+        mrg_probe<<<1, 256, 0, s>>>(buf, res, kProbeIters);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(out, res, sizeof out, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) {
+        mrg_set_error(cudaGetErrorString(e));
+        return MR_ERR_CUDA;
+    }
+    for (int i = 0; i < 3; ++i) cycles[i] = (double)out[i] / kProbeIters;
+    return MR_OK;
 }
 
 mr_status mr_stats(mr_ctx *c, unsigned long long *updates, unsigned long long *steps, long long *leaves) {

@@ -29,6 +29,7 @@
 #pragma once
 #include <cuda_runtime.h>
 
+#include <atomic>
 #include <cstdint>
 
 #include "mr_common.h"
@@ -175,7 +176,7 @@ struct TeamSmem {
     float eps_f[MAXLEV + 1], big_f[MAXLEV + 1];
     double mass[3];
     double audit;
-    unsigned long long updates, steps;
+    unsigned long long updates, steps, passes;
     int cur, nleaf, status, near_ties;
     uint32_t deplev[2];  // levels holding transfer (0) / ghost (1) cells that wait on the same list
     int idx;
@@ -526,7 +527,10 @@ struct Worker {
             collide<T, NF>(d, f);
     }
 
+    // team barrier; every one ends a pass whose results the next pass reads
+    // (counted, so a step's chain of dependent passes can be measured)
     __device__ __forceinline__ void sync() const {
+        if (tid == 0) ++sm.passes;
         if constexpr (WARP)
             __syncwarp();
         else
@@ -1830,6 +1834,7 @@ struct Worker {
             sm.near_ties = 0;
             sm.updates = 0ULL;
             sm.steps = 0ULL;
+            sm.passes = 0ULL;
         }
         sync();
     }
@@ -1884,6 +1889,7 @@ __device__ void load_instance(TeamSmem<T> &sm, const InstDesc &dg, int tid) {
         sm.deplev[1] = st.deplev[1];
         sm.updates = st.updates;
         sm.steps = st.steps;
+        sm.passes = st.passes;
         sm.audit = st.audit;
         for (int j = 0; j < 3; ++j) sm.mass[j] = st.mass[j];
 #ifdef MRG_PHASE_TIMERS
@@ -1929,6 +1935,7 @@ __device__ void store_instance(TeamSmem<T> &sm, int tid) {
         st.deplev[1] = sm.deplev[1];
         st.updates = sm.updates;
         st.steps = sm.steps;
+        st.passes = sm.passes;
         st.audit = sm.audit;
         for (int j = 0; j < 3; ++j) st.mass[j] = sm.mass[j];
 #ifdef MRG_PHASE_TIMERS
@@ -2054,9 +2061,15 @@ __global__ void __launch_bounds__(NT, MINB) mr_persistent(LaunchArgs a) {
         return (int)cudaFuncSetAttribute(mrg::mr_persistent<T, NT, M, K>,                         \
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024); \
     }                                                                                             \
+    /* the attribute belongs to the current device: raised once per device ordinal */             \
     static int mrg_attr_##TAG() {                                                                 \
-        static int rc = mrg_allow_##TAG<MINB, mrg::K_FAST>() | mrg_allow_##TAG<MINB_G, mrg::K_GENERAL>() | \
-                        mrg_allow_##TAG<MINB_S, mrg::K_SCALAR>() | mrg_allow_##TAG<MINB_R, mrg::K_RECOLL>(); \
+        static std::atomic<int> done[64];                                                         \
+        int dev = 0;                                                                              \
+        if (cudaGetDevice(&dev) != cudaSuccess) return (int)cudaErrorInvalidDevice;                \
+        if (dev >= 0 && dev < 64 && done[dev].load(std::memory_order_acquire)) return 0;          \
+        int rc = mrg_allow_##TAG<MINB, mrg::K_FAST>() | mrg_allow_##TAG<MINB_G, mrg::K_GENERAL>() | \
+                 mrg_allow_##TAG<MINB_S, mrg::K_SCALAR>() | mrg_allow_##TAG<MINB_R, mrg::K_RECOLL>(); \
+        if (!rc && dev >= 0 && dev < 64) done[dev].store(1, std::memory_order_release);            \
         return rc;                                                                                \
     }                                                                                             \
     template <int M, int K>                                                                       \

@@ -15,6 +15,7 @@
 #include <cstdint>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 
 #include "../../include/mrlbm.h"
 #include "mr_common.h"
@@ -29,9 +30,37 @@ static __device__ __align__(256) unsigned char g_scratch[MR_STATIC_SCRATCH_BYTES
 
 // Device address of g_scratch per device ordinal, looked up once per device
 // with that device current.  In host code `g_scratch` only names a host-side
-// stand-in, never the device memory, so it is never passed to a kernel.
+// stand-in, never the device memory, so it is never passed to a kernel.  The
+// look-up is guarded by a mutex: host threads making their first call on a
+// device at the same time see one look-up and the same address.
 constexpr int kMaxDevices = 64;
 unsigned char *g_scratch_dev[kMaxDevices] = {nullptr};
+std::mutex g_scratch_mu;
+
+cudaError_t scratch_address(int dev, unsigned char **out) {
+    std::lock_guard<std::mutex> lock(g_scratch_mu);
+    if (!g_scratch_dev[dev]) {
+        void *p = nullptr;
+        const cudaError_t e = cudaGetSymbolAddress(&p, g_scratch);
+        if (e != cudaSuccess) return e;
+        if (!p) return cudaErrorInvalidSymbol;
+        g_scratch_dev[dev] = (unsigned char *)p;
+    }
+    *out = g_scratch_dev[dev];
+    return cudaSuccess;
+}
+
+// Host copies of the reconstruction tables, built on first use (a function-local
+// static: its initialisation is thread-safe).
+struct HostTables {
+    Tables<double> td;
+    Tables<float> tf;
+    HostTables() { mrg_tables(&td, &tf); }
+};
+const HostTables &host_tables() {
+    static const HostTables t;
+    return t;
+}
 
 size_t align256(size_t x) { return (x + 255) / 256 * 256; }
 
@@ -53,7 +82,7 @@ extern "C" mr_status mr_run_static(const mr_instance_desc *desc, int precision, 
     const mr_instance_desc &d = *desc;
     const int nf = nfields(d.eq);
     if (d.Jmin < 2 || d.Jmax < d.Jmin || d.Jmax > MAXLEV || d.gamma < 1 || d.gamma > 3 || nf == 0 || d.mu_bar < 0 ||
-        (d.bc != MR_BC_PERIODIC && d.bc != MR_BC_COPY) || !(d.eps >= 0.0) || !(d.b > d.a) || !(d.lambda > 0.0))
+        (d.bc != MR_BC_PERIODIC && d.bc != MR_BC_COPY) || !(d.eps >= 0.0) || !(d.b > d.a) || !(d.lambda >= 0x1p-16 && d.lambda <= 0x1p16))
         return fail(MR_ERR_ARG, "mr_run_static: invalid instance description");
     for (int j = 0; j < mrg_nrates(d.eq); ++j)
         if (!(d.s[j] > 0.0 && d.s[j] <= 2.0)) return fail(MR_ERR_ARG, "mr_run_static: relaxation rate outside (0, 2]");
@@ -63,6 +92,15 @@ extern "C" mr_status mr_run_static(const mr_instance_desc *desc, int precision, 
         return fail(MR_ERR_ARG, "mr_run_static: the D1Q3 / D1Q5 schemes are built with gamma = 1");
     const bool fp32 = precision == MR_FP32_MIXED;
     cudaStream_t s = (cudaStream_t)stream;
+    // The descriptor is uploaded from host memory that does not outlive this
+    // call, and `updates` waits for the stream: neither belongs in a graph.
+    {
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        const cudaError_t e = cudaStreamIsCapturing(s, &cs);
+        if (e != cudaSuccess) return fail(MR_ERR_CUDA, "mr_run_static: cudaStreamIsCapturing failed (%lld)", (long long)e);
+        if (cs != cudaStreamCaptureStatusNone)
+            return fail(MR_ERR_STATE, "mr_run_static: the stream is capturing; this call cannot be recorded in a graph");
+    }
 
     // layout of the scratch area for this instance (same regions as a bound context)
     const int q = mrg_npop(d.eq);
@@ -100,13 +138,11 @@ extern "C" mr_status mr_run_static(const mr_instance_desc *desc, int precision, 
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices)
         return fail(MR_ERR_CUDA, "mr_run_static: no usable current device");
-    if (!g_scratch_dev[dev]) {
-        void *p = nullptr;
-        cudaError_t e = cudaGetSymbolAddress(&p, g_scratch);
-        if (e != cudaSuccess || !p) return fail(MR_ERR_CUDA, "mr_run_static: cudaGetSymbolAddress failed (%lld)", (long long)e);
-        g_scratch_dev[dev] = (unsigned char *)p;
+    unsigned char *base = nullptr;
+    {
+        const cudaError_t e = scratch_address(dev, &base);
+        if (e != cudaSuccess) return fail(MR_ERR_CUDA, "mr_run_static: cudaGetSymbolAddress failed (%lld)", (long long)e);
     }
-    unsigned char *base = g_scratch_dev[dev];
 
     // descriptor with absolute pointers into the scratch area
     InstDesc h;
@@ -143,13 +179,8 @@ extern "C" mr_status mr_run_static(const mr_instance_desc *desc, int precision, 
     h.lists = (uint32_t *)(base + oL);
     for (int L = 0; L < NLIST; ++L) h.list_off[L] = list_off[L];
     h.st = (InstState *)(base + oState);
-    static Tables<double> td;  // host copies of the reconstruction tables
-    static Tables<float> tf;
-    static bool tables_made = false;
-    if (!tables_made) {
-        mrg_tables(&td, &tf);
-        tables_made = true;
-    }
+    const Tables<double> &td = host_tables().td;
+    const Tables<float> &tf = host_tables().tf;
     // Pageable host sources: cudaMemcpyAsync returns once they are staged, so
     // the stack copies may go out of scope afterwards.  The state and the queue
     // must start at zero; every other byte the kernel reads it writes first.

@@ -84,3 +84,18 @@ def relerr(a, b):
     a, b = np.asarray(a, np.float64), np.asarray(b, np.float64)
     scale = max(1.0, float(np.max(np.abs(b))) if b.size else 1.0)
     return float(np.max(np.abs(a - b))) / scale if a.size else 0.0
+
+
+def prescribed_detail_state(Jmin, Jmax, bc, q, details, base=0.5, other=0.25):
+    """Full tree whose population 0 has exactly the given details
+    {(level, pair p): d} on a constant coarse average (dyadic values, so the
+    multiresolution round trip is exact); the other populations are constant."""
+    off = O.level_offsets(Jmin, Jmax)
+    S = off[Jmax + 1]
+    packed = np.zeros(S)
+    packed[off[Jmin]:off[Jmin + 1]] = base
+    for (l, p), d in details.items():
+        packed[off[l] + 2 * p] = d
+    vals = np.full((q, S), other)
+    vals[0, off[Jmax]:] = O.mr_decode(Jmin, Jmax, 1, bc, packed)
+    return np.ones(S, np.uint8), vals
