@@ -222,10 +222,13 @@ mr_status mr_step_passes(mr_ctx *ctx, int inst, unsigned long long *steps, unsig
 /* Latency probe (no counterpart in the paper): one block hands a value from
  * one warp to another through memory and a block barrier, as consecutive
  * passes of the step do, and times it in SM clock cycles on the current
- * device: cycles[0] per hand-over through global memory, cycles[1] through
- * shared memory, cycles[2] per bare block barrier.  scratch: caller-owned
- * device memory of at least 4096 bytes (256-byte aligned); synchronises the
- * stream. */
+ * device: cycles[0] per hand-over through global memory (a line the block has
+ * read before), cycles[1] through shared memory, cycles[2] per bare block
+ * barrier, cycles[3] through a global line the block has not touched before
+ * (0 unless scratch holds more than 4096 + 256 bytes: one 128-byte line per
+ * hand-over after the first 4096 bytes, up to 4096 of them).  scratch:
+ * caller-owned device memory of at least 4096 bytes (256-byte aligned), all
+ * of it overwritten; cycles: 4 host doubles; synchronises the stream. */
 mr_status mr_probe_latency(void *scratch, size_t bytes, void *stream, double *cycles);
 
 /* Launch shape: threads per block (128, 256, 512 or 1024; one block advances
@@ -272,7 +275,7 @@ mr_status mr_reconstruction_coefficients(int dj, int kind, double *out);
 /* Tracing: SM clock cycles spent by instance inst in each phase of the step,
  * accumulated since its initial state, in the order
  *   projection (adapt), details + threshold, enlargement, grading + marking,
- *   grading of the levels of at most 32 cells, reserved (zero), list
+ *   grading of the levels of at most 32 cells, candidate mask words, list
  *   compaction, data transfer, collision, projection (step), ghosts,
  *   reconstruction, stream + audit
  * (n >= 13 slots).  Only a library compiled with MRG_PHASE_TIMERS records

@@ -36,17 +36,20 @@ def _desc(inst: "workloads.Instance") -> capi.mr_instance_desc:
 
 def probe_latency(device: str = "cuda:0") -> dict:
     """SM cycles of one warp-to-warp hand-over through global memory, through
-    shared memory, and of a bare block barrier (mr_probe_latency)."""
+    shared memory, of a bare block barrier, and through a global line the
+    block has not touched before (mr_probe_latency)."""
     import torch
 
     lib = capi.load()
     dev = torch.device(device)
-    scratch = torch.empty(4096, dtype=torch.uint8, device=dev)
+    nbytes = 4096 + 4096 * 128
+    scratch = torch.empty(nbytes, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream(dev)
-    out = (ctypes.c_double * 3)()
-    capi.check(None, lib.mr_probe_latency(ctypes.c_void_p(scratch.data_ptr()), 4096,
+    out = (ctypes.c_double * 4)()
+    capi.check(None, lib.mr_probe_latency(ctypes.c_void_p(scratch.data_ptr()), nbytes,
                                           ctypes.c_void_p(stream.cuda_stream), out))
-    return {"global_handover_cycles": out[0], "shared_handover_cycles": out[1], "barrier_cycles": out[2]}
+    return {"global_handover_cycles": out[0], "shared_handover_cycles": out[1], "barrier_cycles": out[2],
+            "fresh_line_handover_cycles": out[3]}
 
 
 class MRLBM:

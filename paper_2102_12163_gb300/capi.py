@@ -71,7 +71,7 @@ _lib = None
 
 
 PHASES = ["projection (adapt)", "details + threshold", "enlargement", "grading + marking",
-          "grading (small levels)", "reserved", "list compaction", "data transfer", "collision",
+          "grading (small levels)", "candidate words", "list compaction", "data transfer", "collision",
           "projection (step)", "ghosts", "reconstruction", "stream + audit"]
 
 

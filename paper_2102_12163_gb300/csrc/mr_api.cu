@@ -76,19 +76,37 @@ int nwords_h(int l) { return l >= 5 ? (1 << (l - 5)) : 1; }
 int variant_of(int eq) { return eq == MR_EQ_SW_D1Q3 ? 4 : eq == MR_EQ_SW_D1Q5 ? 5 : nfields_of(eq); }
 // Group of the queue order an instance belongs to, most work per instance
 // first: gamma = 2, 3 (general kernel); gamma = 1 with the reconstructed
-// collision; gamma = 1 with the leaves collision (fast kernel, or the scalar
+// collision; gamma = 1 with the leaves collision and at least CW_MIN_WORDS
+// mask words per bitmask (the fast code with candidate words); the other
+// gamma = 1 instances with the leaves collision (fast kernel, or the scalar
 // kernel when every instance of the group has one field).
-constexpr int NGROUP = 3;
-int group_of(const InstDesc &h) { return h.gamma > 1 ? 0 : h.collision != 0 ? 1 : 2; }
+constexpr int NGROUP = 4;
+int group_of(const InstDesc &h) {
+    return h.gamma > 1 ? 0 : h.collision != 0 ? 1 : h.Wtot >= CW_MIN_WORDS ? 2 : 3;
+}
+// kernel variant of a lone instance
+int kind_of(const InstDesc &h) {
+    return h.gamma > 1 ? K_GENERAL : h.collision != 0 ? K_RECOLL : h.Wtot >= CW_MIN_WORDS ? K_LARGE : K_FAST;
+}
 
 thread_local std::string g_create_error;
 
+// shared-memory entries per cell list at most: shared memory is carved out of
+// the SM's L1, which keeps the population values of the resident instances
+// between passes; on the Jmax 8..14 batch 256 entries per list ran 2 % faster
+// than none, 1024 and 4096 entries 4 % and 7 % slower (one box)
+constexpr int kListEntries = 256;
+
 // Latency probe: warps 0 and 1 of one block alternately read the value the
 // other wrote and write the next one, with a block barrier after every
-// hand-over; through global memory (buf[0..63]), through shared memory, and
-// bare barriers.  Every index stays inside buf[0..63] and the shared array.
+// hand-over; through global memory (buf[0..63], lines the block has read
+// before), through shared memory, bare barriers, and through global memory
+// where every hand-over uses a line no thread of the block has touched
+// (fresh[i * 32], i < nfresh, one 128-byte line each).  Every index stays
+// inside buf[0..63], fresh[0 .. 32 nfresh) and the shared array.
 constexpr int kProbeIters = 4096;
-__global__ void mrg_probe(int *buf, unsigned long long *res, int iters) {
+constexpr size_t kProbeFreshOff = 4096;  // bytes of scratch before the fresh lines
+__global__ void mrg_probe(int *buf, unsigned long long *res, int iters, int *fresh, int nfresh) {
     __shared__ int sh[64];
     if (threadIdx.x < 64) sh[threadIdx.x] = 0;
     __syncthreads();
@@ -106,10 +124,17 @@ __global__ void mrg_probe(int *buf, unsigned long long *res, int iters) {
     long long t2 = clock64();
     for (int i = 0; i < iters; ++i) __syncthreads();
     long long t3 = clock64();
+    // fresh lines: hand-over i writes line i + 1 after reading line i
+    for (int i = 0; i + 1 < nfresh; ++i) {
+        if (me == ((i & 1) ? 32 : 0)) fresh[(i + 1) * 32] = fresh[i * 32] + 1;
+        __syncthreads();
+    }
+    long long t4 = clock64();
     if (me == 0) {
         res[0] = (unsigned long long)(t1 - t0);
         res[1] = (unsigned long long)(t2 - t1) + (unsigned long long)(sh[iters & 63] & 0);
         res[2] = (unsigned long long)(t3 - t2);
+        res[3] = nfresh > 1 ? (unsigned long long)(t4 - t3) / (unsigned long long)(nfresh - 1) : 0ull;
     }
 }
 
@@ -133,10 +158,11 @@ struct mr_ctx {
     bool bound = false, initialised = false;
     int block = 0, grid_req = 0, sms = 0;
     int grid[NKIND] = {};      // blocks per launch, by kernel variant (K_*)
-    int mask_cap[NKIND] = {};  // words per bitmask a block team keeps in shared memory, by variant
-    int wmax = 0;              // mask words of the largest instance
-    int n_group[3] = {};       // instances per group of the queue order (group_of)
-    int group_kind[3] = {K_GENERAL, K_RECOLL, K_FAST};  // kernel variant of each group
+    int mask_cap[NKIND] = {};  // mask-region words a block team keeps in shared memory, by variant
+    int list_cap[NKIND] = {};  // shared-memory words for the first entries of the cell lists, by variant
+    int wmax = 0;              // mask-region words of the largest instance
+    int n_group[NGROUP] = {};  // instances per group of the queue order (group_of)
+    int group_kind[NGROUP] = {K_GENERAL, K_RECOLL, K_LARGE, K_FAST};  // kernel variant of each group
     // The groups run as separate kernels; a second stream lets one group's
     // kernel fill the SMs that another's tail leaves idle (fork and join by events).
     cudaStream_t side = nullptr;
@@ -203,7 +229,7 @@ static void layout(mr_ctx *c) {
     c->off_ident = o;
     o = align_up(o + sizeof(int) * n);
     c->off_queue = o;
-    o = align_up(o + sizeof(int) * 64);
+    o = align_up(o + sizeof(int) * 16 * NKIND);  // one queue counter per kernel variant, 64 bytes apart
     c->off_tab = o;
     o = align_up(o + sizeof(Tables<double>) + sizeof(Tables<float>));
     c->m_off.assign(n, 0);
@@ -222,8 +248,11 @@ static void layout(mr_ctx *c) {
         InstDesc &h = c->hdesc[i];
         int nf = nfields_of(d.eq), q = npop_of(d.eq);
         long long S = (1LL << (d.Jmax + 1)) - (1LL << d.Jmin), N = 1LL << d.Jmax;
-        int W = 0;
-        for (int l = d.Jmin; l <= d.Jmax; ++l) W += nwords_h(l);
+        int W = 0, OW = 0;
+        for (int l = d.Jmin; l <= d.Jmax; ++l) {
+            W += nwords_h(l);
+            OW += occ_words_of(l);
+        }
         h.Jmin = d.Jmin;
         h.Jmax = d.Jmax;
         h.bc = d.bc;
@@ -240,6 +269,7 @@ static void layout(mr_ctx *c) {
             if (fr == 0.5 && e2 - 1 >= -16 && e2 - 1 <= 16) h.lam_log2 = e2 - 1;
         }
         h.Wtot = W;
+        h.OW = OW;
         h.eps = d.eps;
         h.a = d.a;
         h.b = d.b;
@@ -253,7 +283,7 @@ static void layout(mr_ctx *c) {
         c->inst_off[i] = o;
         size_t vb = c->vbytes();
         size_t oV = 0, oPhi = align_up(oV + vb * q * S), oM = align_up(oPhi + vb * q * (N + 1));
-        size_t oL = align_up(oM + sizeof(uint32_t) * NMASK * W);
+        size_t oL = align_up(oM + sizeof(uint32_t) * (size_t)mask_region_words(W, OW));
         // every list holds distinct cells of the instance, so S entries always suffice
         long long caps[NLIST] = {S, S, S, S};
         long long lo = 0;
@@ -353,6 +383,7 @@ static int launch_group(mr_ctx *c, int phases, int nsteps, const int *order, int
     a.aux1 = aux1;
     a.tables = c->ws + c->off_tab + (c->fp32() ? sizeof(Tables<double>) : 0);
     a.smem_mask_words = c->mask_cap[kind];
+    a.smem_list_words = c->list_cap[kind];
     int rc = c->cuda(cudaMemsetAsync(a.queue, 0, sizeof(int), stream), "cudaMemsetAsync");
     if (rc) return rc;
     int grid = std::min(a.n, c->grid[kind]);
@@ -376,7 +407,7 @@ static int launch(mr_ctx *c, int phases, int nsteps, int only_inst, const void *
     if (!c->bound) return c->fail(MR_ERR_STATE, "context not bound to a workspace");
     if (only_inst >= 0) {
         const InstDesc &h = c->hdesc[only_inst];
-        const int kind = h.gamma > 1 ? K_GENERAL : h.collision != 0 ? K_RECOLL : K_FAST;
+        const int kind = kind_of(h);
         return launch_group(c, phases, nsteps, (const int *)(c->ws + c->off_ident) + only_inst, 1, kind, aux0, aux1,
                             c->stream, c->prio_least);
     }
@@ -529,10 +560,18 @@ static int configure(mr_ctx *c) {
         // the resident blocks a variant is compiled for share the SM's 227 KB
         const int minb = std::max(1, mrg_min_blocks(c->fp32(), c->block, kind));
         size_t budget = c->n() == 1 ? 220u * 1024u : (227u * 1024u) / (size_t)minb - 1024u;
-        int fit = budget > base ? (int)((budget - base) / (NMASK * sizeof(uint32_t))) : 0;
-        c->mask_cap[kind] = std::min(c->wmax, fit);
+        int fit = budget > base ? (int)((budget - base) / sizeof(uint32_t)) : 0;
+        // the mask region of the largest instance when it fits (a batch keeps the
+        // area for the instances that fit; a lone instance that does not fit
+        // leaves it empty); the rest holds the first entries of the cell lists
+        int mc = std::min(c->wmax, fit);
+        if (c->n() == 1 && c->wmax > fit) mc = 0;
+        int lw = std::min(fit - mc, NLIST * kListEntries);
+        lw = std::max(0, lw / NLIST * NLIST);
+        c->mask_cap[kind] = mc;
+        c->list_cap[kind] = lw;
         int nb = 0;
-        int rc = c->cuda((cudaError_t)mrg_occupancy(c->fp32(), c->block, kind, c->mask_cap[kind], &nb), "occupancy");
+        int rc = c->cuda((cudaError_t)mrg_occupancy(c->fp32(), c->block, kind, mc + lw, &nb), "occupancy");
         if (rc) return rc;
         c->grid[kind] = c->grid_req > 0 ? c->grid_req : std::max(1, nb) * c->sms;
     }
@@ -562,12 +601,12 @@ static int upload_order(mr_ctx *c) {
     bool scalar_only = true;  // every gamma = 1 leaves-collision instance has one field
     for (int i = 0; i < n; ++i) {
         ++c->n_group[group_of(dd[i])];
-        if (group_of(dd[i]) == 2 && variant_of(dd[i].eq) != 1) scalar_only = false;
+        if (group_of(dd[i]) == 3 && variant_of(dd[i].eq) != 1) scalar_only = false;
     }
     // A mixed group stays in one fast kernel: split into fast and scalar
     // kernels on two streams it ran 2 % faster or 5 % slower than one kernel,
     // depending on which kernel's blocks reached the SMs first.
-    c->group_kind[2] = scalar_only ? K_SCALAR : K_FAST;
+    c->group_kind[3] = scalar_only ? K_SCALAR : K_FAST;
     return c->cuda(cudaMemcpyAsync(c->ws + c->off_order, c->order_host.data(), sizeof(int) * n, cudaMemcpyHostToDevice,
                                    c->stream),
                    "upload");
@@ -629,7 +668,7 @@ mr_status mr_bind(mr_ctx *c, void *ws, size_t bytes, void *stream) {
         return (mr_status)rc;
     if ((rc = c->cuda(cudaStreamSynchronize(s), "cudaStreamSynchronize"))) return (mr_status)rc;
     c->wmax = 0;
-    for (int i = 0; i < n; ++i) c->wmax = std::max(c->wmax, dd[i].Wtot);
+    for (int i = 0; i < n; ++i) c->wmax = std::max(c->wmax, (int)smem_region_words(dd[i].Wtot, dd[i].OW));
     if ((rc = configure(c))) return (mr_status)rc;
     c->bound = true;
     c->initialised = false;
@@ -898,12 +937,16 @@ mr_status mr_probe_latency(void *scratch, size_t bytes, void *stream, double *cy
         return MR_ERR_ARG;
     }
     cudaStream_t s = (cudaStream_t)stream;
-    unsigned long long out[3] = {0, 0, 0};
+    unsigned long long out[4] = {0, 0, 0, 0};
     int *buf = (int *)scratch;
     unsigned long long *res = (unsigned long long *)((unsigned char *)scratch + 2048);
-    cudaError_t e = cudaMemsetAsync(scratch, 0, 4096, s);
+    // fresh 128-byte lines after the first 4096 bytes, as many as fit (at most kProbeIters)
+    const size_t nlines = bytes > kProbeFreshOff ? (bytes - kProbeFreshOff) / 128 : 0;
+    const int nfresh = (int)(nlines < (size_t)kProbeIters ? nlines : (size_t)kProbeIters);
+    int *fresh = (int *)((unsigned char *)scratch + kProbeFreshOff);
+    cudaError_t e = cudaMemsetAsync(scratch, 0, bytes, s);
     if (e == cudaSuccess) {
-        mrg_probe<<<1, 256, 0, s>>>(buf, res, kProbeIters);
+        mrg_probe<<<1, 256, 0, s>>>(buf, res, kProbeIters, fresh, nfresh);
         e = cudaGetLastError();
     }
     if (e == cudaSuccess) e = cudaMemcpyAsync(out, res, sizeof out, cudaMemcpyDeviceToHost, s);
@@ -913,6 +956,7 @@ mr_status mr_probe_latency(void *scratch, size_t bytes, void *stream, double *cy
         return MR_ERR_CUDA;
     }
     for (int i = 0; i < 3; ++i) cycles[i] = (double)out[i] / kProbeIters;
+    cycles[3] = (double)out[3];
     return MR_OK;
 }
 

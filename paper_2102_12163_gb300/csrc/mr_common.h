@@ -8,7 +8,10 @@
 //          finest-lattice interface they belong to; also the staging area of
 //          the initial data
 //   masks  NMASK bitmasks over all cells of all levels, 32 cells per word,
-//          level l at words [woff_l, woff_l + max(1, 2^l / 32))
+//          level l at words [woff_l, woff_l + max(1, 2^l / 32)); then the
+//          candidate-word list of the step (Wtot entries at most) and two
+//          occupancy bitmaps (one per tree buffer) with one bit per mask
+//          word, level l at occupancy words [ooff_l, ooff_l + max(1, W_l / 32))
 //   lists  compacted cell lists (entry = level << KBITS | index), sorted by
 //          level then index; per-level segments in InstState::seg
 //   state  InstState
@@ -42,7 +45,7 @@ enum { PH_INIT_FULL = 1, PH_INIT_STATE = 2, PH_ADAPT = 4, PH_STEP = 8, PH_FINEST
 enum { ST_NONFINITE = 1, ST_FLUXED = 2 };
 // phases timed by the profiling build (MRG_PHASE_TIMERS)
 enum {
-    T_UPSWEEP_A = 0, T_DETAILS, T_ENLARGE, T_GRADE, T_GRADE_SMALL, T_RESERVED, T_LISTS, T_TRANSFER,
+    T_UPSWEEP_A = 0, T_DETAILS, T_ENLARGE, T_GRADE, T_GRADE_SMALL, T_CANDIDATES, T_LISTS, T_TRANSFER,
     T_COLLIDE, T_UPSWEEP_S, T_GHOSTS, T_RECON, T_STREAM, NPHASE
 };
 
@@ -67,6 +70,7 @@ struct InstDesc {
     int collision;         // 0: leaves collision, 1: reconstructed collision (Section 4.5)
     int lam_log2;          // k when lambda = 2^k exactly (|k| <= 16), else NOT_POW2
     int Wtot;              // mask words over all levels
+    int OW;                // occupancy words over all levels (one bit per mask word)
     double eps, a, b, lam, eqp;
     double s[3];
     long long S;           // cells over all levels
@@ -85,7 +89,31 @@ struct InstDesc {
     // correctly rounded reciprocal of lambda, for the FP64 division by lambda
     // with one correction step (see the kernel's div_lam)
     double rlam;
+    // constant factors of the collision, rounded once in the path's precision
+    // exactly as the per-cell expressions would round them: 1 - s[j]; Euler
+    // 1.5 - 0.5 gamma_gas, gamma_gas - 1, 0.5 (1 - gamma_gas); shallow water 0.5 g
+    double oms[3], eu_a, eu_b, eu_c, sw_g2;
+    float oms_f[3], eu_a_f, eu_b_f, eu_c_f, sw_g2_f;
 };
+
+// words of the mask region of an instance: NMASK bitmasks, the candidate-word
+// list and two occupancy bitmaps
+inline long long mask_region_words(int Wtot, int OW) { return (long long)(NMASK + 1) * Wtot + 2LL * OW; }
+// Instances with at least this many mask words per bitmask run their word
+// passes over the step's candidate words; smaller ones visit every word, which
+// costs less than building the candidate list (measured on the Jmax 8..14 batch
+// and the single instances).
+constexpr int CW_MIN_WORDS = 2048;
+// words of the mask region a block keeps in shared memory: without candidate
+// words the list and the occupancy bitmaps are not used
+#ifdef __CUDACC__
+__host__ __device__
+#endif
+inline long long smem_region_words(int Wtot, int OW) {
+    return Wtot >= CW_MIN_WORDS ? (long long)(NMASK + 1) * Wtot + 2LL * OW : (long long)NMASK * Wtot;
+}
+// occupancy words of one level: one bit per mask word of the level
+inline int occ_words_of(int l) { return l >= 10 ? (1 << (l - 10)) : 1; }
 
 // fills InstDesc's float copies of lam, eqp, s and minv (host side, after those are set)
 inline void fill_float_constants(InstDesc &h) {
@@ -95,6 +123,18 @@ inline void fill_float_constants(InstDesc &h) {
     for (int i = 0; i < 5; ++i)
         for (int j = 0; j < 5; ++j) h.minv_f[i][j] = (float)h.minv[i][j];
     h.rlam = 1.0 / h.lam;  // IEEE division: correctly rounded
+    for (int j = 0; j < 3; ++j) {
+        h.oms[j] = 1.0 - h.s[j];
+        h.oms_f[j] = 1.0f - h.s_f[j];
+    }
+    h.eu_a = 1.5 - 0.5 * h.eqp;
+    h.eu_b = h.eqp - 1.0;
+    h.eu_c = 0.5 * (1.0 - h.eqp);
+    h.sw_g2 = 0.5 * h.eqp;
+    h.eu_a_f = 1.5f - 0.5f * h.eqp_f;
+    h.eu_b_f = h.eqp_f - 1.0f;
+    h.eu_c_f = 0.5f * (1.0f - h.eqp_f);
+    h.sw_g2_f = 0.5f * h.eqp_f;
 }
 
 // Reconstruction tables for gamma = 1, indexed by the level gap dj = Jmax - l
@@ -128,7 +168,8 @@ struct LaunchArgs {
     const void *aux0;     // phase input / output (see the kernel)
     const void *aux1;
     const void *tables;   // Tables<T> in device memory
-    int smem_mask_words;  // block teams keep their bitmasks in shared memory when Wtot <= this
+    int smem_mask_words;  // block teams keep their mask region in shared memory when it has at most this many words
+    int smem_list_words;  // shared-memory words after the mask area holding the first entries of the NLIST cell lists
     int kind;             // kernel variant (K_*) the launch runs
 };
 
@@ -137,8 +178,11 @@ struct LaunchArgs {
 // K_FAST with one conserved field (D1Q2), compiled on their own for a higher
 // residency; K_RECOLL: gamma = 1 with the reconstructed collision, the code of
 // K_GENERAL compiled for a residency of its own (its dense reconstruction gains
-// from blocks in flight, the wide stencils from registers).
-constexpr int K_FAST = 0, K_GENERAL = 1, K_SCALAR = 2, K_RECOLL = 3, NKIND = 4;
+// from blocks in flight, the wide stencils from registers); K_LARGE: the code of
+// K_FAST for the instances with at least CW_MIN_WORDS mask words per bitmask,
+// whose word passes visit the step's candidate words (the code that builds
+// them stays out of K_FAST and K_SCALAR, which it slowed down).
+constexpr int K_FAST = 0, K_GENERAL = 1, K_SCALAR = 2, K_RECOLL = 3, K_LARGE = 4, NKIND = 5;
 
 }  // namespace mrg
 

@@ -171,6 +171,9 @@ template <typename T>
 struct TeamSmem {
     InstDesc d;
     int woff[MAXLEV + 2];
+    int ooff[MAXLEV + 2];    // occupancy words of level l start at ooff[l]
+    int cw_seg[MAXLEV + 2];  // candidate words of level l: entries [cw_seg[l], cw_seg[l+1]) of the list
+    int sparse;              // word passes over candidate words (else over every word)
     int seg[NLIST][MAXLEV + 2];
     double eps_l[MAXLEV + 1], big_l[MAXLEV + 1], dx_l[MAXLEV + 1];  // per level
     float eps_f[MAXLEV + 1], big_f[MAXLEV + 1];
@@ -253,6 +256,19 @@ template <typename T>
 __device__ __forceinline__ T minv_of(const InstDesc &d, int h, int i) {
     if constexpr (sizeof(T) == 8) return d.minv[h][i]; else return d.minv_f[h][i];
 }
+// 1 - s[i] and the equilibria's constant factors, rounded once on the host
+template <typename T>
+__device__ __forceinline__ T oms_of(const InstDesc &d, int i) {
+    if constexpr (sizeof(T) == 8) return d.oms[i]; else return d.oms_f[i];
+}
+template <typename T>
+__device__ __forceinline__ void eq_consts(const InstDesc &d, T &a, T &b, T &c, T &g2) {
+    if constexpr (sizeof(T) == 8) {
+        a = d.eu_a; b = d.eu_b; c = d.eu_c; g2 = d.sw_g2;
+    } else {
+        a = d.eu_a_f; b = d.eu_b_f; c = d.eu_c_f; g2 = d.sw_g2_f;
+    }
+}
 
 // x / lambda for a lambda that is no power of two, in FP64 bit for bit the
 // correctly rounded quotient without a division: q0 = RN(x r) with r = RN(1 / lambda) is
@@ -272,26 +288,31 @@ __device__ __forceinline__ T div_lam(T x, const InstDesc &d) {
     }
 }
 
+// equilibria of the relaxed moments; the constant factors (0.5 g, 1.5 - 0.5
+// gamma_gas, gamma_gas - 1, 0.5 (1 - gamma_gas)) come rounded from the host,
+// the same values the expressions would give per cell
 template <typename T, int NF>
-__device__ __forceinline__ void equilibria(int eq, T eqp, const T *mc, T *meq) {
+__device__ __forceinline__ void equilibria(const InstDesc &d, T eqp, const T *mc, T *meq) {
     using A = Ar<T>;
+    T ca, cb, cc, g2;
+    eq_consts<T>(d, ca, cb, cc, g2);
     if constexpr (NF == 1) {
-        if (eq == 0)
+        if (d.eq == 0)
             meq[0] = A::mul(eqp, mc[0]);  // advection: c m0
         else
             meq[0] = half_of<T>(A::mul(mc[0], mc[0]));  // Burgers: m0^2 / 2
     } else if constexpr (NF == 2) {
         // shallow water (h, hu): hu, hu^2 / h + g h^2 / 2
         meq[0] = mc[1];
-        meq[1] = A::add(A::div(A::mul(mc[1], mc[1]), mc[0]), A::mul(A::mul(T(0.5), eqp), A::mul(mc[0], mc[0])));
+        meq[1] = A::add(A::div(A::mul(mc[1], mc[1]), mc[0]), A::mul(g2, A::mul(mc[0], mc[0])));
     } else {
         // Euler (rho, rho u, E), Section 5.3
         T gg = eqp;
         T u2 = A::mul(mc[1], mc[1]);
         meq[0] = mc[1];
-        meq[1] = A::add(A::mul(A::sub(T(1.5), A::mul(T(0.5), gg)), A::div(u2, mc[0])), A::mul(A::sub(gg, T(1)), mc[2]));
+        meq[1] = A::add(A::mul(ca, A::div(u2, mc[0])), A::mul(cb, mc[2]));
         meq[2] = A::add(A::mul(gg, A::div(A::mul(mc[2], mc[1]), mc[0])),
-                        A::mul(A::mul(T(0.5), A::sub(T(1), gg)), A::div(A::mul(u2, mc[1]), A::mul(mc[0], mc[0]))));
+                        A::mul(cc, A::div(A::mul(u2, mc[1]), A::mul(mc[0], mc[0]))));
     }
 }
 
@@ -306,11 +327,11 @@ __device__ __forceinline__ void collide(const InstDesc &d, T *f) {
         mc[i] = A::add(f[2 * i], f[2 * i + 1]);
         mn[i] = A::mul(lam, A::sub(f[2 * i], f[2 * i + 1]));
     }
-    equilibria<T, NF>(d.eq, eqp_of<T>(d), mc, meq);
+    equilibria<T, NF>(d, eqp_of<T>(d), mc, meq);
 #pragma unroll
     for (int i = 0; i < NF; ++i) {
         T s = s_of<T>(d, i);
-        T mstar = A::add(A::mul(A::sub(T(1), s), mn[i]), A::mul(s, meq[i]));
+        T mstar = A::add(A::mul(oms_of<T>(d, i), mn[i]), A::mul(s, meq[i]));
         // m*/lambda: an exact power-of-two scaling when lambda = 2^k (same value as the division)
         T g = d.lam_log2 != NOT_POW2 ? scale2(mstar, -d.lam_log2) : div_lam<T>(mstar, d);
         f[2 * i] = half_of<T>(A::add(mc[i], g));
@@ -323,7 +344,7 @@ template <int NF>
 __device__ __forceinline__ void equilibrium_populations(const InstDesc &d, const double *mc, double *f) {
     using A = Ar<double>;
     double meq[NF];
-    equilibria<double, NF>(d.eq, d.eqp, mc, meq);
+    equilibria<double, NF>(d, d.eqp, mc, meq);
 #pragma unroll
     for (int i = 0; i < NF; ++i) {
         double g = A::div(meq[i], d.lam);
@@ -356,7 +377,9 @@ __device__ __forceinline__ void dq_collide(const InstDesc &d, T *f) {
         }
     }
     T meq[Q];
-    meq[2] = (m[1] * m[1]) / m[0] + (T(0.5) * eqp_of<T>(d)) * (m[0] * m[0]);
+    T ca, cb, cc, g2;
+    eq_consts<T>(d, ca, cb, cc, g2);
+    meq[2] = (m[1] * m[1]) / m[0] + g2 * (m[0] * m[0]);
     if constexpr (Q == 5) {
         meq[3] = (lam * lam) * m[1];
         meq[4] = (lam * lam) * meq[2];
@@ -489,13 +512,64 @@ __device__ __noinline__ T edge_walk(const T *rowbase, int Jmin, int Jmax, int bc
     return w[C];
 }
 
+// NaN or infinity, from the exponent field (integer units)
+__device__ __forceinline__ bool nonfinite(double x) { return (__double2hiint(x) & 0x7FF00000) == 0x7FF00000; }
+__device__ __forceinline__ bool nonfinite(float x) { return (__float_as_uint(x) & 0x7F800000u) == 0x7F800000u; }
+
+// ---------------------------------------------------------------------------
+// FP64 threshold decisions on bit patterns.  Non-negative doubles order as
+// their bit patterns, so max |d| over the populations and its comparisons with
+// eps_l and the Harten level run on the integer units instead of GB300's
+// scarce FP64 pipe, with the same outcome as the floating-point max and >=
+// (a NaN detail is skipped, as fmax skips it).
+__device__ __forceinline__ unsigned long long abs_bits(double x) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x) & 0x7FFFFFFFFFFFFFFFull;
+    return b > 0x7FF0000000000000ull ? 0ull : b;
+}
+// keep / refine decisions of a pair with max |detail| bits Db, and whether it
+// lies within 1e-12 relative of eps_l or of the Harten level: an integer
+// pre-filter (1e-12 relative is at most 9008 units in the last place) and the
+// exact test behind it
+__device__ __forceinline__ void decide_bits(unsigned long long Db, double el, double bl, bool hasref, bool &keepit,
+                                            bool &refit, bool &tie) {
+    const unsigned long long eb = (unsigned long long)__double_as_longlong(el),
+                             bb = (unsigned long long)__double_as_longlong(bl);
+    keepit = Db >= eb;
+    refit = hasref && Db >= bb;
+    const long long de = (long long)(Db - eb), db = (long long)(Db - bb);
+    tie = false;
+    if ((de < 16384 && de > -16384) || (hasref && db < 16384 && db > -16384)) {
+        const double D = __longlong_as_double((long long)Db);
+        tie = fabs(D - el) <= 1e-12 * el || (hasref && fabs(D - bl) <= 1e-12 * bl);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// A compacted cell list: its first `cap` entries in shared memory (written and
+// read within the block at shared-memory latency), the rest in global memory
+// at the same positions.
+struct ListView {
+    uint32_t *s;  // shared-memory part
+    uint32_t *g;  // global list (all positions)
+    int cap;
+    __device__ __forceinline__ uint32_t operator[](int i) const { return i < cap ? s[i] : g[i]; }
+    __device__ __forceinline__ void put(int i, uint32_t v) const {
+        if (i < cap)
+            s[i] = v;
+        else
+            g[i] = v;
+    }
+};
+
 // ---------------------------------------------------------------------------
 // the instance worker; TS threads (a warp or the whole block) form the team
 
 constexpr int QMAX = 6;  // populations of the largest scheme (vectorial D1Q2^3)
 
 // WIDE: prediction stencils gamma = 2, 3 (the gamma = 1 code is a separate instantiation)
-template <typename T, int NF, int TS, bool WIDE>
+// SPM: word passes over candidate words never (0), for the instances with at
+// least CW_MIN_WORDS words per bitmask (1), always (2)
+template <typename T, int NF, int TS, bool WIDE, int SPM>
 struct Worker {
     static constexpr bool WARP = TS == 32;
     // NF = 1, 2, 3: vectorial D1Q2^NF; NF = 4: D1Q3, NF = 5: D1Q5 shallow water
@@ -510,13 +584,19 @@ struct Worker {
     T *V;
     T *Phi;
     uint32_t *M;  // mask base (shared memory when the masks fit, else global)
+    uint32_t *SL; // shared-memory parts of the cell lists (lcap entries each)
+    int lcap;
     int tid;      // rank in the team
+    mutable unsigned npass = 0;  // team barriers of this launch (added to the instance's count at its end)
 
-    __device__ Worker(TeamSmem<T> &s, const Tables<T> &tb, BlockScratch &x, int rank, uint32_t *masks)
+    __device__ Worker(TeamSmem<T> &s, const Tables<T> &tb, BlockScratch &x, int rank, uint32_t *masks, uint32_t *slist,
+                      int list_cap)
         : sm(s), tab(tb), bx(x), d(s.d), tid(rank) {
         V = (T *)d.V;
         Phi = (T *)d.Phi;
         M = masks;
+        SL = slist;
+        lcap = slist ? list_cap : 0;
     }
 
     // leaves collision of the q populations of one cell
@@ -530,7 +610,7 @@ struct Worker {
     // team barrier; every one ends a pass whose results the next pass reads
     // (counted, so a step's chain of dependent passes can be measured)
     __device__ __forceinline__ void sync() const {
-        if (tid == 0) ++sm.passes;
+        ++npass;
         if constexpr (WARP)
             __syncwarp();
         else
@@ -552,7 +632,24 @@ struct Worker {
     }
 
     __device__ __forceinline__ uint32_t *mask(int m) { return M + (long long)m * d.Wtot; }
-    __device__ __forceinline__ uint32_t *list(int L) { return d.lists + d.list_off[L]; }
+    // candidate-word list of the step (global mask word indices, sorted by level then word)
+    __device__ __forceinline__ uint32_t *cwl() { return M + (long long)NMASK * d.Wtot; }
+    // i-th word of the step's word passes: a candidate word, or word i itself
+    __device__ __forceinline__ int cw_at(int i) { return sparse_on() ? (int)cwl()[i] : i; }
+    __device__ __forceinline__ bool sparse_on() const {
+        if constexpr (SPM == 0)
+            return false;
+        else if constexpr (SPM == 2)
+            return true;
+        else
+            return sm.sparse != 0;
+    }
+    // occupancy bitmap of tree buffer b (M_R0 or M_R1): bit wi & 31 of word ooff[l] + (wi >> 5) is set
+    // when word wi of level l of that tree holds a cell
+    __device__ __forceinline__ uint32_t *occ(int b) { return M + (long long)(NMASK + 1) * d.Wtot + (long long)b * d.OW; }
+    __device__ __forceinline__ ListView list(int L) {
+        return ListView{SL + (long long)L * lcap, d.lists + d.list_off[L], lcap};
+    }
     __device__ __forceinline__ T *row(int h, int l) { return V + (long long)h * d.S + cell_off(l, d.Jmin); }
 
     // sums over the team of nf per-thread doubles, valid in thread 0 (one barrier)
@@ -627,7 +724,7 @@ struct Worker {
     }
 
     // ---- projection of the internal cells of level l (Def. Projection operator)
-    __device__ __forceinline__ void project_level(const uint32_t *lst, int l) {
+    __device__ __forceinline__ void project_level(const ListView &lst, int l) {
         int b = sm.seg[L_INT][l], e = sm.seg[L_INT][l + 1];
         for (int i = b + tid; i < e; i += TS) {
             long long k = lst[i] & KMASK;
@@ -643,7 +740,7 @@ struct Worker {
 
     // ---- S1: leaves collision (eq. LeavesCollision) ---------------------------
     __device__ void collide_all() {
-        const uint32_t *lst = list(L_LEAF);
+        const ListView lst = list(L_LEAF);
         for (int i = tid; i < sm.nleaf; i += TS) {
             uint32_t ent = lst[i];
             int l = ent >> KBITS;
@@ -669,7 +766,9 @@ struct Worker {
                 h = h + g[c];
                 hu = hu + ((T)dq_w(c) * lam) * g[c];
             }
-            meq[0] = (hu * hu) / h + (T(0.5) * eqp_of<T>(d)) * (h * h);
+            T ca, cb, cc, g2;
+            eq_consts<T>(d, ca, cb, cc, g2);
+            meq[0] = (hu * hu) / h + g2 * (h * h);
             if constexpr (q == 5) {
                 meq[1] = (lam * lam) * hu;
                 meq[2] = (lam * lam) * meq[0];
@@ -679,7 +778,7 @@ struct Worker {
             T mc[NF];
 #pragma unroll
             for (int i = 0; i < NF; ++i) mc[i] = A::add(g[2 * i], g[2 * i + 1]);
-            equilibria<T, NF>(d.eq, eqp_of<T>(d), mc, meq);
+            equilibria<T, NF>(d, eqp_of<T>(d), mc, meq);
         }
     }
 
@@ -706,7 +805,7 @@ struct Worker {
         constexpr int NR = DQ ? q - 2 : nf;  // relaxed moments
         constexpr int NWARP = TS / 32;
         const int lane = tid & 31, warp = tid >> 5;
-        const uint32_t *leaves = list(L_LEAF);
+        const ListView leaves = list(L_LEAF);
         const long long stride = d.N + 1;
         for (int i = warp; i < sm.nleaf; i += NWARP) {
             const uint32_t ent = leaves[i];
@@ -775,7 +874,7 @@ struct Worker {
                 for (int j = 0; j < NF; ++j) {
                     const T mc = A::add(f[2 * j], f[2 * j + 1]), mn = A::mul(lam, A::sub(f[2 * j], f[2 * j + 1]));
                     const T sj = s_of<T>(d, j);
-                    const T mstar = A::add(A::mul(A::sub(T(1), sj), mn), A::mul(sj, mavg[j]));
+                    const T mstar = A::add(A::mul(oms_of<T>(d, j), mn), A::mul(sj, mavg[j]));
                     const T g = d.lam_log2 != NOT_POW2 ? scale2(mstar, -d.lam_log2) : div_lam<T>(mstar, d);
                     f[2 * j] = half_of<T>(A::add(mc, g));
                     f[2 * j + 1] = half_of<T>(A::sub(mc, g));
@@ -790,7 +889,7 @@ struct Worker {
 
     // ---- A1 / S2: projection sweep, fine to coarse ---------------------------
     __device__ void upsweep() {
-        const uint32_t *li = list(L_INT);
+        const ListView li = list(L_INT);
         for (int l = d.Jmax - 1; l >= d.Jmin; --l) {
             if (sm.seg[L_INT][l] == sm.seg[L_INT][l + 1]) continue;
             project_level(li, l);
@@ -808,7 +907,7 @@ struct Worker {
     // therefore equals the level-by-level projection of the streamed leaves up
     // to rounding, and replaces its Jmax - Jmin dependent passes.
     __device__ void project_by_flux() {
-        const uint32_t *li = list(L_INT);
+        const ListView li = list(L_INT);
         const int b = sm.seg[L_INT][d.Jmin], e = sm.seg[L_INT][d.Jmax];
         for (int i = b + tid; i < e; i += TS) {
             const uint32_t ent = li[i];
@@ -841,7 +940,7 @@ struct Worker {
             return;
         }
         // the even cells of the tree above Jmin: first children 2p of the internal cells p
-        const uint32_t *lst = list(L_INT);
+        const ListView lst = list(L_INT);
         int b = sm.seg[L_INT][d.Jmin], e = sm.seg[L_INT][d.Jmax];
         uint32_t *keep = mask(M_KEEP), *ref = mask(M_REF);
         for (int i = b + tid; i < e; i += TS) {
@@ -852,18 +951,16 @@ struct Worker {
             long long pl = wrapc(p - 1, l - 1, d.bc), pr = wrapc(p + 1, l - 1, d.bc);
             bool keepit, refit, tie = false;
             if constexpr (sizeof(T) == 8) {
-                double D = 0.0;
+                unsigned long long Db = 0ull;
 #pragma unroll
                 for (int h = 0; h < QMAX; ++h)
                     if (h < q) {
                         const T *rc = row(h, l - 1);
-                        double dv = row(h, l)[k] - (rc[p] + C1 * (rc[pr] - rc[pl]));
-                        D = fmax(D, fabs(dv));
+                        const double dv = row(h, l)[k] - (rc[p] + C1 * (rc[pr] - rc[pl]));
+                        const unsigned long long b = abs_bits(dv);
+                        Db = b > Db ? b : Db;
                     }
-                double el = sm.eps_l[l], bl = sm.big_l[l];
-                keepit = D >= el;
-                refit = hasref && D >= bl;
-                tie = fabs(D - el) <= 1e-12 * el || (hasref && fabs(D - bl) <= 1e-12 * bl);
+                decide_bits(Db, sm.eps_l[l], sm.big_l[l], hasref, keepit, refit, tie);
             } else {
                 float D = 0.0f, B = 0.0f;
 #pragma unroll
@@ -910,7 +1007,7 @@ struct Worker {
     // the number of operations, (6 gamma + 2) u times the sum of |inputs|
     // (3 gamma + 1 roundings, each at most u times that sum, with a factor 2 margin)
     __device__ __noinline__ void details_wide() {
-        const uint32_t *lst = list(L_INT);  // first children 2p of the internal cells p
+        const ListView lst = list(L_INT);  // first children 2p of the internal cells p
         const int b = sm.seg[L_INT][d.Jmin], e = sm.seg[L_INT][d.Jmax], g = d.gamma;
         const T *c = tab.pc[g];
         uint32_t *keep = mask(M_KEEP), *ref = mask(M_REF);
@@ -921,6 +1018,7 @@ struct Worker {
             const long long p = ent & KMASK, k = 2 * p;
             bool keepit, refit, tie = false;
             double Dd = 0.0;
+            unsigned long long Db = 0ull;
             float Df = 0.0f, B = 0.0f;
             for (int h = 0; h < q; ++h) {
                 const T *rc = row(h, l - 1);
@@ -933,17 +1031,15 @@ struct Worker {
                 }
                 const T vk = row(h, l)[k], vp = rc[p];
                 if constexpr (sizeof(T) == 8) {
-                    Dd = fmax(Dd, fabs(vk - (vp + sum)));
+                    const unsigned long long b = abs_bits(vk - (vp + sum));
+                    Db = b > Db ? b : Db;
                 } else {
                     Df = fmaxf(Df, fabsf(vk - (vp + sum)));
                     B = fmaxf(B, fabsf(vk) + fabsf(vp) + mag);
                 }
             }
             if constexpr (sizeof(T) == 8) {
-                const double el = sm.eps_l[l], bl = sm.big_l[l];
-                keepit = Dd >= el;
-                refit = hasref && Dd >= bl;
-                tie = fabs(Dd - el) <= 1e-12 * el || (hasref && fabs(Dd - bl) <= 1e-12 * bl);
+                decide_bits(Db, sm.eps_l[l], sm.big_l[l], hasref, keepit, refit, tie);
             } else {
                 B *= (float)(6 * g + 2) * 0x1p-24f;
                 const float el = sm.eps_f[l], bl = sm.big_f[l];
@@ -977,10 +1073,97 @@ struct Worker {
         }
     }
 
-    // ---- A3: R(H(T)) per word ------------------------------------------------
+    // ---- candidate words of the step -----------------------------------------
+    // Every cell of the new tree lies within 2 gamma + 4 cells of a cell of the
+    // old tree on its level or of a child of one (the enlargement moves at most
+    // sigma + 1 <= 3 cells from a kept cell and adds children of kept pairs;
+    // grading from level l + 1 reaches gamma + 2 cells beyond half of that
+    // level's distance), and every transfer or ghost mark lies within
+    // 2 gamma + 10 <= 16 cells of one: inside the mask words next to (+-1 word)
+    // a word that holds an old cell, or a child word of one.  Those words are
+    // the step's candidates.  The word passes (enlargement, grading and
+    // marking, list compaction, clearing) visit them only; every other word of
+    // every mask stays zero.  The list is built from the occupancy bitmap of
+    // the old tree (one bit per mask word) by a block scan.
+
+    // level l and index j within the level of occupancy word og (levels up to 9
+    // have one occupancy word, level l >= 10 has 2^(l - 10))
+    __device__ __forceinline__ void level_of_occ(int og, int &l, int &j) const {
+        const int nsmall = max(0, min(d.Jmax, 9) - d.Jmin + 1);
+        if (og < nsmall) {
+            l = d.Jmin + og;
+            j = 0;
+            return;
+        }
+        const int L0 = d.Jmin > 10 ? d.Jmin : 10;
+        const int x = og - nsmall + (1 << (L0 - 10));
+        l = 10 + (31 - __clz(x));
+        j = x - (1 << (l - 10));
+    }
+    // candidate bits of occupancy word j of level l, from the old tree's occupancy oc
+    __device__ __forceinline__ uint32_t cand_bits(const uint32_t *oc, int l, int j) const {
+        const int Lo = l >= 5 ? l - 5 : 0;  // the level's mask words: 2^Lo
+        const uint32_t vb = Lo >= 5 ? FULL : ((1u << (1 << Lo)) - 1u);
+        if (l <= 6) return vb;  // levels of at most two words: every word
+        const uint32_t *ol = oc + sm.ooff[l];
+        uint32_t x = dilate([&](int q) { return ol[q]; }, Lo, j, 1, d.bc);
+        if (l > d.Jmin) {
+            // child words of the occupied words of level l - 1
+            const uint32_t *op = oc + sm.ooff[l - 1];
+            x |= dilate([&](int q) { return Lo > 5 ? spread16(op[q >> 1] >> (16 * (q & 1))) : (spread16(op[0]) & vb); },
+                        Lo, j, 1, d.bc);
+        }
+        return x & vb;
+    }
+
+    __device__ void build_cw() {
+        constexpr int NW = TS / 32;
+        const int lane = tid & 31, warp = tid >> 5;
+        const uint32_t *oc = occ(sm.cur);
+        uint32_t *cw = cwl();
+        const int OW = d.OW;
+        int run = 0;
+        for (int r = 0, base = 0; base < OW; ++r, base += TS) {
+            const int og = base + tid;
+            int l = d.Jmin, j = 0;
+            uint32_t c = 0u;
+            if (og < OW) {
+                level_of_occ(og, l, j);
+                c = cand_bits(oc, l, j);
+            }
+            const int cnt = __popc(c);
+            int x = cnt;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int y = __shfl_up_sync(FULL, x, o);
+                if (lane >= o) x += y;
+            }
+            int *sw = bx.scan_w[r & 1][0];  // alternate buffers: one barrier per round
+            if (lane == 31) sw[warp] = x;
+            sync();
+            const int v = lane < NW ? sw[lane] : 0;
+            const int before = __reduce_add_sync(FULL, lane < warp ? v : 0);
+            const int tot = __reduce_add_sync(FULL, v);
+            int off = run + before + x - cnt;
+            if (og < OW && j == 0) sm.cw_seg[l] = off;
+            const uint32_t g0 = (uint32_t)(sm.woff[l] + 32 * j);
+            while (c) {
+                const int b = __ffs(c) - 1;
+                c &= c - 1u;
+                cw[off++] = g0 + (uint32_t)b;
+            }
+            run += tot;
+        }
+        if (tid == 0) sm.cw_seg[d.Jmax + 1] = run;
+        sync();
+    }
+
+    // ---- A3: R(H(T)) per candidate word --------------------------------------
     __device__ void enlarge(uint32_t *Rn) {
         const uint32_t *keep = mask(M_KEEP), *ref = mask(M_REF);
-        for (int g = tid; g < d.Wtot; g += TS) {
+        const int ncw = sm.cw_seg[d.Jmax + 1];
+        for (int i = tid; i < ncw; i += TS) {
+            const int g = cw_at(i);
             int l, wi;
             level_of_word(sm, g, l, wi);
             uint32_t vb = valid_bits(l), rh;
@@ -1016,14 +1199,16 @@ struct Worker {
             if (grade && l > d.Jmin + 1) {
                 uint32_t *rp = Rn + sm.woff[l - 1];
                 if constexpr (!WIDE) {
-                    for (int wp = tid; wp < (Wl >> 1); wp += TS) {
+                    for (int i = sm.cw_seg[l - 1] + tid; i < sm.cw_seg[l]; i += TS) {
+                        const int wp = cw_at(i) - sm.woff[l - 1];
                         uint32_t x = fold2(rl[2 * wp], rl[2 * wp + 1]);
                         bool eL = (word_bc(rl, 2 * wp - 1, Wl, d.bc) >> 30) != 0u;  // children of parent 32 wp - 1
                         bool eR = (word_bc(rl, 2 * wp + 2, Wl, d.bc) & 3u) != 0u;   // children of parent 32 wp + 32
                         rp[wp] |= pairexpand(dilate1_edges(x, eL, eR));
                     }
                 } else {
-                    for (int wp = tid; wp < (Wl >> 1); wp += TS) {
+                    for (int i = sm.cw_seg[l - 1] + tid; i < sm.cw_seg[l]; i += TS) {
+                        const int wp = cw_at(i) - sm.woff[l - 1];
                         const uint32_t x = fold2(rl[2 * wp], rl[2 * wp + 1]);
                         // parents 29..31 of the word on the left, 0..2 of the word on the right
                         const uint32_t xl = fold3(word_bc(rl, 2 * wp - 1, Wl, d.bc) >> 26) << 29;
@@ -1034,8 +1219,10 @@ struct Worker {
             }
             const uint32_t *rol = Ro + sm.woff[l];
             uint32_t *lfl = LF + sm.woff[l], *prl = PR + sm.woff[l], *ghl = GH + sm.woff[l];
+            const int cb = sm.cw_seg[l], ce = sm.cw_seg[l + 1], wo = sm.woff[l];
             if (l == d.Jmax) {
-                for (int wi = tid; wi < Wl; wi += TS) {
+                for (int i = cb + tid; i < ce; i += TS) {
+                    const int wi = cw_at(i) - wo;
                     uint32_t r = rl[wi];
                     lfl[wi] = r;
                     prl[wi] = r & ~rol[wi];
@@ -1044,7 +1231,8 @@ struct Worker {
             } else if constexpr (WIDE) {
                 const int Wc = Wl << 1;
                 const uint32_t *rc = Rn + sm.woff[l + 1], *pc = PR + sm.woff[l + 1], *gc = GH + sm.woff[l + 1];
-                for (int wi = tid; wi < Wl; wi += TS) {
+                for (int i = cb + tid; i < ce; i += TS) {
+                    const int wi = cw_at(i) - wo;
                     const uint32_t r = rl[wi], ro = rol[wi];
                     const uint32_t lf = r & ~fold2(rc[2 * wi], rc[2 * wi + 1]);
                     // leaf bits of the 16 cells of each neighbouring word next to this one
@@ -1065,7 +1253,8 @@ struct Worker {
             } else {
                 const int Wc = Wl << 1;
                 const uint32_t *rc = Rn + sm.woff[l + 1], *pc = PR + sm.woff[l + 1], *gc = GH + sm.woff[l + 1];
-                for (int wi = tid; wi < Wl; wi += TS) {
+                for (int i = cb + tid; i < ce; i += TS) {
+                    const int wi = cw_at(i) - wo;
                     uint32_t r = rl[wi], ro = rol[wi];
                     uint32_t lf = r & ~fold2(rc[2 * wi], rc[2 * wi + 1]);
                     // leaf bits of cells 30, 31 of the left word and 0, 1 of the right word
@@ -1178,24 +1367,29 @@ struct Worker {
         m[L_GH] = mask(M_GH)[g];
     }
 
-    // Rounds of TS consecutive mask words, one word per thread; a block scan of
-    // the per-word counts places each word's entries (the lists stay sorted by
-    // level, then cell).  A dense word costs its owner at most 32 stores per
-    // list, and dense levels are spread over as many threads as they have words.
-    __device__ void build_lists(const uint32_t *Rn) {
+    // Rounds of TS consecutive candidate words, one word per thread; a block
+    // scan of the per-word counts places each word's entries (the lists stay
+    // sorted by level, then cell).  A dense word costs its owner at most 32
+    // stores per list, and dense levels are spread over as many threads as they
+    // have words.  The occupancy bitmap occn of the listed tree is set on the
+    // way (it must start cleared).
+    __device__ void build_lists(const uint32_t *Rn, uint32_t *occn) {
         constexpr int NW = TS / 32;
         const int lane = tid & 31, warp = tid >> 5;
-        const int Wtot = d.Wtot;
+        const int ncw = sm.cw_seg[d.Jmax + 1];
+        const bool sparse = sparse_on();
         int run[NLIST] = {0, 0, 0, 0};
         if (tid == 0) sm.deplev[0] = sm.deplev[1] = 0u;  // new lists: gathered again by predict_fill
-        for (int r = 0, base = 0; base < Wtot; ++r, base += TS) {
-            const int g = base + tid;
-            const bool valid = g < Wtot;
+        for (int r = 0, base = 0; base < ncw; ++r, base += TS) {
+            const int i = base + tid;
+            const bool valid = i < ncw;
             int l = 0, wi = 0;
             uint32_t m[NLIST] = {0u, 0u, 0u, 0u};
             if (valid) {
+                const int g = cw_at(i);
                 level_of_word(sm, g, l, wi);
                 word_lists(Rn, g, l, m);
+                if (sparse && (m[L_INT] | m[L_LEAF])) atomicOr(&occn[sm.ooff[l] + (wi >> 5)], 1u << (wi & 31));
             }
             int inc[NLIST];
 #pragma unroll
@@ -1221,12 +1415,17 @@ struct Worker {
                 const int tot = __reduce_add_sync(FULL, v);
                 uint32_t x = m[L];
                 int off = run[L] + before + inc[L] - __popc(x);
-                if (valid && wi == 0) sm.seg[L][l] = off;
-                uint32_t *dst = list(L);
+                if (valid && i == sm.cw_seg[l]) {
+                    // first candidate word of level l; levels just below without
+                    // candidate words hold no cell and start at the same place
+                    sm.seg[L][l] = off;
+                    for (int k = l - 1; k >= d.Jmin && sm.cw_seg[k] == sm.cw_seg[l]; --k) sm.seg[L][k] = off;
+                }
+                const ListView dst = list(L);
                 while (x) {
                     const int bit = __ffs(x) - 1;
                     x &= x - 1u;
-                    dst[off++] = pk + (uint32_t)bit;
+                    dst.put(off++, pk + (uint32_t)bit);
                 }
                 run[L] += tot;
             }
@@ -1234,6 +1433,10 @@ struct Worker {
         if (tid == 0) {
 #pragma unroll
             for (int L = 0; L < NLIST; ++L) sm.seg[L][d.Jmax + 1] = run[L];
+            // the finest levels without candidate words are empty
+            for (int k = d.Jmax; k >= d.Jmin && sm.cw_seg[k] == ncw; --k)
+#pragma unroll
+                for (int L = 0; L < NLIST; ++L) sm.seg[L][k] = run[L];
             sm.nleaf = run[L_LEAF];
         }
         sync();
@@ -1282,7 +1485,7 @@ struct Worker {
     // coarse to fine, on the levels that have any.  The marks of both lists stay
     // in their masks until the next step's A2 clears them.
     __device__ void predict_fill(int L) {
-        const uint32_t *lst = list(L);
+        const ListView lst = list(L);
         const uint32_t *P = mask(L == L_GH ? M_GH : M_PRED);
         const int slot = L == L_GH ? 1 : 0;
         const int b = sm.seg[L][d.Jmin + 1], e = sm.seg[L][d.Jmax + 1];
@@ -1310,16 +1513,25 @@ struct Worker {
     __device__ void adapt() {
         uint32_t *Ro = mask(sm.cur), *Rn = mask(sm.cur ^ 1);
         tick(NPHASE);
+        if (sparse_on()) build_cw();
         {
             // the transfer / ghost marks of the last list compaction share storage
-            // with KEEP / REF, which A2 accumulates into: clear them (the barrier of
-            // A1 orders this before A2)
+            // with KEEP / REF, which A2 accumulates into: clear them (all of them
+            // lie in candidate words; the barrier of A1 orders this before A2),
+            // and the occupancy bitmap the list compaction will fill
             uint32_t *pr = mask(M_PRED), *gh = mask(M_GH);
-            for (int g = tid; g < d.Wtot; g += TS) {
+            const int ncw = sm.cw_seg[d.Jmax + 1];
+            for (int i = tid; i < ncw; i += TS) {
+                const int g = cw_at(i);
                 pr[g] = 0u;
                 gh[g] = 0u;
             }
+            if (sparse_on()) {
+                uint32_t *on = occ(sm.cur ^ 1);
+                for (int g = tid; g < d.OW; g += TS) on[g] = 0u;
+            }
         }
+        tick(T_CANDIDATES);
         if (!DQ && (sm.status & ST_FLUXED))
             project_by_flux();
         else
@@ -1334,9 +1546,17 @@ struct Worker {
         tick(T_ENLARGE);
         grade_and_mark(Rn, Ro, true);
         tick(T_GRADE_SMALL);
-        build_lists(Rn);
+        build_lists(Rn, occ(sm.cur ^ 1));
         tick(T_LISTS);
         predict_fill(L_PRED);
+        if (sparse_on()) {
+            // the old tree's buffer holds the next step's new tree: clear it (its
+            // cells lie in candidate words; nothing reads it after the grading);
+            // without candidate words the enlargement writes every word
+            const uint32_t *cw = cwl();
+            const int ncw = sm.cw_seg[d.Jmax + 1];
+            for (int i = tid; i < ncw; i += TS) Ro[cw[i]] = 0u;
+        }
         tick(T_TRANSFER);
         if (tid == 0) {
             sm.cur ^= 1;
@@ -1383,7 +1603,7 @@ struct Worker {
             }
         }
         const uint32_t *R = mask(sm.cur);
-        const uint32_t *leaves = list(L_LEAF);
+        const ListView leaves = list(L_LEAF);
         for (int i = tid; i < sm.nleaf; i += TS) {
             uint32_t ent = leaves[i];
             int l = ent >> KBITS;
@@ -1415,15 +1635,15 @@ struct Worker {
                     rfirst = rlast = r[k];
                 } else {
                     T vm1 = r[wrapc(k - 1, l, d.bc)], v0 = r[k], vp1 = r[wrapc(k + 1, l, d.bc)];
-                    T tt = T(C1) * (vp1 - vm1);
-                    T pe = v0 + tt, po = v0 - tt;  // children of the leaf
                     const T *rf = row(h, l + 1);
                     if (need_first) {
                         if (at_left) {
                             rfirst = bf[0] * v0 + bf[1] * vp1;
                         } else if (fin_l) {
+                            // next to a finer neighbour: the leaf's own children (predicted) enter
+                            const T tt = T(C1) * (vp1 - vm1);
                             long long c = 2 * wrapc(k - 1, l, d.bc);
-                            rfirst = dot4(t1[0], rf[c], t1[1], rf[c + 1], t1[2], pe, t1[3], po);
+                            rfirst = dot4(t1[0], rf[c], t1[1], rf[c + 1], t1[2], v0 + tt, t1[3], v0 - tt);
                         } else {
                             rfirst = dot4(cf[0], r[wrapc(k - 2, l, d.bc)], cf[1], vm1, cf[2], v0, cf[3], vp1);
                         }
@@ -1432,8 +1652,9 @@ struct Worker {
                         if (at_right) {
                             rlast = bf[0] * v0 + bf[1] * vm1;
                         } else if (fin_r) {
+                            const T tt = T(C1) * (vp1 - vm1);
                             long long c = 2 * wrapc(k + 1, l, d.bc);
-                            rlast = dot4(t1[3], pe, t1[2], po, t1[1], rf[c], t1[0], rf[c + 1]);
+                            rlast = dot4(t1[3], v0 + tt, t1[2], v0 - tt, t1[1], rf[c], t1[0], rf[c + 1]);
                         } else {
                             rlast = dot4(cf[3], vm1, cf[2], v0, cf[1], vp1, cf[0], r[wrapc(k + 2, l, d.bc)]);
                         }
@@ -1457,7 +1678,7 @@ struct Worker {
     // values by the level-by-level reconstruction (edge_walk) instead of tables
     __device__ __noinline__ void reconstruct_wide() {
         const uint32_t *R = mask(sm.cur);
-        const uint32_t *leaves = list(L_LEAF);
+        const ListView leaves = list(L_LEAF);
         const int g = d.gamma;
         const T *c = tab.pc[g];
         for (int i = tid; i < sm.nleaf; i += TS) {
@@ -1504,7 +1725,7 @@ struct Worker {
     // second-cell tables.
     __device__ __noinline__ void reconstruct_dq() {
         const uint32_t *R = mask(sm.cur);
-        const uint32_t *leaves = list(L_LEAF);
+        const ListView leaves = list(L_LEAF);
         for (int i = tid; i < sm.nleaf; i += TS) {
             const uint32_t ent = leaves[i];
             const int l = ent >> KBITS;
@@ -1530,22 +1751,34 @@ struct Worker {
                     continue;
                 }
                 const T vm1 = r[wrapc(k - 1, l, d.bc)], v0 = r[k], vp1 = r[wrapc(k + 1, l, d.bc)];
-                const T tt = T(C1) * (vp1 - vm1);
-                const T pe = v0 + tt, po = v0 - tt;  // children of the leaf
                 const T *rf = row(h, l + 1);
+                // the leaf's own children (predicted), used next to a finer neighbour
+                auto children = [&](T &pe, T &po) {
+                    const T tt = T(C1) * (vp1 - vm1);
+                    pe = v0 + tt;
+                    po = v0 - tt;
+                };
                 // cell `sec` (0: first / last, 1: second from that edge) next to the left or right edge
                 auto from_left = [&](int sec) -> T {
                     const T *bf = sec ? tab.bf2[dj] : tab.bf[dj], *t1 = sec ? tab.t12[dj] : tab.t1[dj],
                             *cf = sec ? tab.cf2[dj] : tab.cf[dj];
                     if (at_left) return bf[0] * v0 + bf[1] * vp1;
-                    if (fin_l) return dot4(t1[0], rf[cl], t1[1], rf[cl + 1], t1[2], pe, t1[3], po);
+                    if (fin_l) {
+                        T pe, po;
+                        children(pe, po);
+                        return dot4(t1[0], rf[cl], t1[1], rf[cl + 1], t1[2], pe, t1[3], po);
+                    }
                     return dot4(cf[0], r[wrapc(k - 2, l, d.bc)], cf[1], vm1, cf[2], v0, cf[3], vp1);
                 };
                 auto from_right = [&](int sec) -> T {
                     const T *bf = sec ? tab.bf2[dj] : tab.bf[dj], *t1 = sec ? tab.t12[dj] : tab.t1[dj],
                             *cf = sec ? tab.cf2[dj] : tab.cf[dj];
                     if (at_right) return bf[0] * v0 + bf[1] * vm1;
-                    if (fin_r) return dot4(t1[3], pe, t1[2], po, t1[1], rf[cr], t1[0], rf[cr + 1]);
+                    if (fin_r) {
+                        T pe, po;
+                        children(pe, po);
+                        return dot4(t1[3], pe, t1[2], po, t1[1], rf[cr], t1[0], rf[cr + 1]);
+                    }
                     return dot4(cf[3], vm1, cf[2], v0, cf[1], vp1, cf[0], r[wrapc(k + 2, l, d.bc)]);
                 };
                 if (w > 0) {
@@ -1566,7 +1799,7 @@ struct Worker {
     // eta = -delta (sigma > 0) or delta - 1 (sigma < 0), V the finest values of
     // reconstruct_dq (wrapped, or clamped at a copy boundary); audit of (h, hu)
     __device__ __noinline__ void stream_dq() {
-        const uint32_t *leaves = list(L_LEAF);
+        const ListView leaves = list(L_LEAF);
         const long long N = d.N;
         auto at = [&](long long i) -> long long { return d.bc == 0 ? (i & (N - 1)) : (i < 0 ? 0 : (i >= N ? N - 1 : i)); };
         double macc[3] = {0.0, 0.0, 0.0};
@@ -1596,7 +1829,7 @@ struct Worker {
                         }
                         v = v + (w > 0 ? wgt : -wgt) * acc;
                     }
-                    bad |= !isfinite(v);
+                    bad |= nonfinite(v);
                     r[k] = v;
                     fn[h] = v;
                 }
@@ -1690,7 +1923,7 @@ struct Worker {
             stream_dq();
             return;
         }
-        const uint32_t *leaves = list(L_LEAF);
+        const ListView leaves = list(L_LEAF);
         double macc[3] = {0.0, 0.0, 0.0};
         float fhi[3] = {0.0f, 0.0f, 0.0f}, flo[3] = {0.0f, 0.0f, 0.0f};
         bool bad = false;
@@ -1710,7 +1943,7 @@ struct Worker {
                     T coef = (h & 1) ? -w : w;
                     T *r = row(h, l);
                     T v = r[k] + coef * (ph[first] - ph[next]);
-                    bad |= !isfinite(v);
+                    bad |= nonfinite(v);
                     r[k] = v;
                     fn[h] = v;
                 }
@@ -1764,6 +1997,7 @@ struct Worker {
             int l, wi;
             level_of_word(sm, g, l, wi);
             R[g] = valid_bits(l);
+            mask(M_R1)[g] = 0u;
             mask(M_KEEP)[g] = 0u;
             mask(M_REF)[g] = 0u;
         }
@@ -1792,6 +2026,7 @@ struct Worker {
             uint32_t w = 0;
             for (int b = 0; b < nb; ++b) w |= (Rb[base + b] ? 1u : 0u) << b;
             R[g] = w;
+            mask(M_R1)[g] = 0u;
             mask(M_KEEP)[g] = 0u;
             mask(M_REF)[g] = 0u;
         }
@@ -1803,10 +2038,23 @@ struct Worker {
 
     __device__ __noinline__ void finish_init() {
         uint32_t *R = mask(sm.cur);
+        {
+            // every mask word is a candidate of this first marking
+            if (sparse_on()) {
+                uint32_t *cw = cwl();
+                for (int g = tid; g < d.Wtot; g += TS) cw[g] = (uint32_t)g;
+                for (int g = tid; g < d.OW; g += TS) {
+                    occ(M_R0)[g] = 0u;
+                    occ(M_R1)[g] = 0u;
+                }
+            }
+            for (int l = d.Jmin + tid; l <= d.Jmax + 1; l += TS) sm.cw_seg[l] = sm.woff[l];
+        }
+        sync();
         grade_and_mark(R, R, false);  // PRED empty: the tree is its own old tree
-        build_lists(R);
+        build_lists(R, occ(sm.cur));
         // FP64 totals of the initial leaves
-        const uint32_t *leaves = list(L_LEAF);
+        const ListView leaves = list(L_LEAF);
         double macc[3] = {0.0, 0.0, 0.0};
         for (int i = tid; i < sm.nleaf; i += TS) {
             uint32_t ent = leaves[i];
@@ -1837,6 +2085,7 @@ struct Worker {
             sm.passes = 0ULL;
         }
         sync();
+        npass = 0;
     }
 
     // ---- multiresolution reconstruction on the finest level (measurement) ----
@@ -1876,7 +2125,7 @@ struct Worker {
 // ---------------------------------------------------------------------------
 // instance state in and out of shared memory (TS threads of the team)
 
-template <typename T, int TS>
+template <typename T, int TS, int SPM>
 __device__ void load_instance(TeamSmem<T> &sm, const InstDesc &dg, int tid) {
     if (tid == 0) {
         sm.d = dg;
@@ -1897,12 +2146,19 @@ __device__ void load_instance(TeamSmem<T> &sm, const InstDesc &dg, int tid) {
         sm.tlast = clock64();
 #endif
         int Jmin = dg.Jmin, Jmax = dg.Jmax;
-        int o = 0;
+        int o = 0, oo = 0;
         for (int l = Jmin; l <= Jmax; ++l) {
             sm.woff[l] = o;
+            sm.ooff[l] = oo;
             o += l >= 5 ? (1 << (l - 5)) : 1;
+            oo += l >= 10 ? (1 << (l - 10)) : 1;
         }
         sm.woff[Jmax + 1] = o;
+        sm.ooff[Jmax + 1] = oo;
+        sm.sparse = (SPM == 2 || (SPM == 1 && dg.Wtot >= CW_MIN_WORDS)) ? 1 : 0;
+        // without candidate words every word of level l is visited
+        if (!sm.sparse)
+            for (int l = Jmin; l <= Jmax + 1; ++l) sm.cw_seg[l] = sm.woff[l];
         sm.g0s = Jmin < 5 ? 5 - Jmin : 0;
         sm.gbase = Jmin < 5 ? 1 : (1 << (Jmin - 5));
     }
@@ -1950,10 +2206,10 @@ __device__ void store_instance(TeamSmem<T> &sm, int tid) {
 }
 
 // one instance for the launch's steps
-template <typename T, int NF, int TS, bool WIDE>
+template <typename T, int NF, int TS, bool WIDE, int SPM>
 __device__ __forceinline__ void run_instance(TeamSmem<T> &sm, const Tables<T> &tab, BlockScratch &bx, const LaunchArgs &a, int tid,
-                             uint32_t *masks) {
-    Worker<T, NF, TS, WIDE> w(sm, tab, bx, tid, masks);
+                             uint32_t *masks, uint32_t *slist, int lcap) {
+    Worker<T, NF, TS, WIDE, SPM> w(sm, tab, bx, tid, masks, slist, lcap);
     if (a.phases & PH_INIT_FULL) w.init_full((const double *)a.aux0 + sm.d.m_off);
     if (a.phases & PH_INIT_STATE) w.init_state((const unsigned char *)a.aux0, (const double *)a.aux1);
     for (int n = 0; n < a.nsteps; ++n) {
@@ -1961,6 +2217,7 @@ __device__ __forceinline__ void run_instance(TeamSmem<T> &sm, const Tables<T> &t
         if (a.phases & PH_STEP) w.lbm_step();
     }
     if (a.phases & PH_FINEST) w.finest((double *)a.aux0);
+    if (tid == 0) sm.passes += w.npass;
 }
 
 // Bitmasks live in shared memory (smask, room for `cap` words per mask) when the
@@ -1968,13 +2225,27 @@ __device__ __forceinline__ void run_instance(TeamSmem<T> &sm, const Tables<T> &t
 // step's predictions read; KEEP / REF share their storage and A2 clears it) are
 // copied in at the start and back at the end; the other masks are rebuilt by
 // every step.
-template <typename T, int TS, bool WIDE, bool SCALAR>
+template <typename T, int TS, bool WIDE, bool SCALAR, int SPM>
 __device__ void run_team(TeamSmem<T> &sm, const Tables<T> &tab, BlockScratch &bx, const LaunchArgs &a,
-                         const InstDesc &dg, int tid, uint32_t *smask, int cap) {
-    load_instance<T, TS>(sm, dg, tid);
-    const int W = sm.d.Wtot;
-    const bool local = smask != nullptr && W <= cap;
+                         const InstDesc &dg, int tid, uint32_t *smask, int cap, uint32_t *slist, int lcap) {
+    load_instance<T, TS, SPM>(sm, dg, tid);
+    // the first lcap entries of every cell list live in shared memory for the launch
+    if (slist)
+        for (int L = 0; L < NLIST; ++L) {
+            const int n = min(lcap, sm.seg[L][sm.d.Jmax + 1]);
+            const uint32_t *gl = sm.d.lists + sm.d.list_off[L];
+            for (int i = tid; i < n; i += TS) slist[L * lcap + i] = gl[i];
+        }
+    const int W = sm.d.Wtot, OW = sm.d.OW;
+    const long long region = smem_region_words(W, OW);
+    const bool local = smask != nullptr && region <= cap;
     uint32_t *masks = local ? smask : sm.d.masks;
+    const long long oo = (long long)(NMASK + 1) * W + (long long)sm.cur * OW;  // occupancy of the current tree
+    if (SPM == 2 || (SPM == 1 && sm.sparse)) {
+        // the other tree buffer starts empty: a step writes its new tree there in candidate words only
+        uint32_t *other = masks + (long long)(sm.cur ^ 1) * W;
+        for (int g = tid; g < W; g += TS) other[g] = 0u;
+    }
     if (local) {
         const uint32_t *gr = sm.d.masks + (long long)sm.cur * W;
         uint32_t *lr = smask + sm.cur * W;
@@ -1984,21 +2255,29 @@ __device__ void run_team(TeamSmem<T> &sm, const Tables<T> &tab, BlockScratch &bx
             smask[M_PRED * W + g] = gp[g];
             smask[M_GH * W + g] = gg[g];
         }
-        __syncthreads();
+        if (SPM == 2 || (SPM == 1 && sm.sparse))
+            for (int g = tid; g < OW; g += TS) smask[oo + g] = sm.d.masks[oo + g];
     }
+    __syncthreads();
     if constexpr (SCALAR) {
-        run_instance<T, 1, TS, WIDE>(sm, tab, bx, a, tid, masks);
+        run_instance<T, 1, TS, WIDE, SPM>(sm, tab, bx, a, tid, masks, slist, lcap);
     } else {
         // scheme variant: D1Q2^nf, or D1Q3 / D1Q5 shallow water (equilibria 4, 5)
         const int var = sm.d.eq == 4 ? 4 : sm.d.eq == 5 ? 5 : sm.d.nf;
         switch (var) {
-        case 1: run_instance<T, 1, TS, WIDE>(sm, tab, bx, a, tid, masks); break;
-        case 2: run_instance<T, 2, TS, WIDE>(sm, tab, bx, a, tid, masks); break;
-        case 4: run_instance<T, 4, TS, WIDE>(sm, tab, bx, a, tid, masks); break;
-        case 5: run_instance<T, 5, TS, WIDE>(sm, tab, bx, a, tid, masks); break;
-        default: run_instance<T, 3, TS, WIDE>(sm, tab, bx, a, tid, masks); break;
+        case 1: run_instance<T, 1, TS, WIDE, SPM>(sm, tab, bx, a, tid, masks, slist, lcap); break;
+        case 2: run_instance<T, 2, TS, WIDE, SPM>(sm, tab, bx, a, tid, masks, slist, lcap); break;
+        case 4: run_instance<T, 4, TS, WIDE, SPM>(sm, tab, bx, a, tid, masks, slist, lcap); break;
+        case 5: run_instance<T, 5, TS, WIDE, SPM>(sm, tab, bx, a, tid, masks, slist, lcap); break;
+        default: run_instance<T, 3, TS, WIDE, SPM>(sm, tab, bx, a, tid, masks, slist, lcap); break;
         }
     }
+    if (slist)
+        for (int L = 0; L < NLIST; ++L) {
+            const int n = min(lcap, sm.seg[L][sm.d.Jmax + 1]);
+            uint32_t *gl = sm.d.lists + sm.d.list_off[L];
+            for (int i = tid; i < n; i += TS) gl[i] = slist[L * lcap + i];
+        }
     if (local) {
         uint32_t *gr = sm.d.masks + (long long)sm.cur * W;
         uint32_t *gp = sm.d.masks + (long long)M_PRED * W, *gg = sm.d.masks + (long long)M_GH * W;
@@ -2008,6 +2287,9 @@ __device__ void run_team(TeamSmem<T> &sm, const Tables<T> &tab, BlockScratch &bx
             gp[g] = smask[M_PRED * W + g];
             gg[g] = smask[M_GH * W + g];
         }
+        const long long oc = (long long)(NMASK + 1) * W + (long long)sm.cur * OW;
+        if (SPM == 2 || (SPM == 1 && sm.sparse))
+            for (int g = tid; g < OW; g += TS) sm.d.masks[oc + g] = smask[oc + g];
     }
     store_instance<T, TS>(sm, tid);
 }
@@ -2022,11 +2304,13 @@ __device__ void run_team(TeamSmem<T> &sm, const Tables<T> &tab, BlockScratch &bx
 template <typename T, int NT, int MINB, int KIND>
 __global__ void __launch_bounds__(NT, MINB) mr_persistent(LaunchArgs a) {
     constexpr bool WIDE = KIND == K_GENERAL || KIND == K_RECOLL;
+    constexpr int SPM = KIND == K_LARGE ? 2 : WIDE ? 1 : 0;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     BlockSmem<T, NT> &bs = *reinterpret_cast<BlockSmem<T, NT> *>(smem_raw);
-    uint32_t *smask = a.smem_mask_words > 0
-                          ? reinterpret_cast<uint32_t *>(smem_raw + ((sizeof(BlockSmem<T, NT>) + 15) / 16) * 16)
-                          : nullptr;
+    uint32_t *sdyn = reinterpret_cast<uint32_t *>(smem_raw + ((sizeof(BlockSmem<T, NT>) + 15) / 16) * 16);
+    uint32_t *smask = a.smem_mask_words > 0 ? sdyn : nullptr;
+    const int lcap = a.smem_list_words / NLIST;
+    uint32_t *slist = lcap > 0 ? sdyn + a.smem_mask_words : nullptr;
     {
         const uint32_t *src = (const uint32_t *)a.tables;
         uint32_t *dst = (uint32_t *)&bs.tab;
@@ -2038,8 +2322,8 @@ __global__ void __launch_bounds__(NT, MINB) mr_persistent(LaunchArgs a) {
         const int idx = bs.idx;
         __syncthreads();
         if (idx >= a.n) return;
-        run_team<T, NT, WIDE, KIND == K_SCALAR>(bs.team, bs.tab, bs.scratch, a, a.descs[a.order[idx]], threadIdx.x, smask,
-                              a.smem_mask_words);
+        run_team<T, NT, WIDE, KIND == K_SCALAR, SPM>(bs.team, bs.tab, bs.scratch, a, a.descs[a.order[idx]], threadIdx.x, smask,
+                                                a.smem_mask_words, slist, lcap);
     }
 }
 
@@ -2054,7 +2338,7 @@ __global__ void __launch_bounds__(NT, MINB) mr_persistent(LaunchArgs a) {
 #define MRG_INSTANTIATE(T, NT, MINB, MINB_S, MINB_G, MINB_R, TAG)                                  \
     static size_t mrg_dyn_##TAG(int mask_words) {                                                 \
         size_t base = (sizeof(mrg::BlockSmem<T, NT>) + 15) / 16 * 16;                              \
-        return base + (size_t)mask_words * mrg::NMASK * sizeof(uint32_t);                          \
+        return base + (size_t)mask_words * sizeof(uint32_t);                                       \
     }                                                                                             \
     template <int M, int K>                                                                       \
     static int mrg_allow_##TAG() {                                                                \
@@ -2068,7 +2352,8 @@ __global__ void __launch_bounds__(NT, MINB) mr_persistent(LaunchArgs a) {
         if (cudaGetDevice(&dev) != cudaSuccess) return (int)cudaErrorInvalidDevice;                \
         if (dev >= 0 && dev < 64 && done[dev].load(std::memory_order_acquire)) return 0;          \
         int rc = mrg_allow_##TAG<MINB, mrg::K_FAST>() | mrg_allow_##TAG<MINB_G, mrg::K_GENERAL>() | \
-                 mrg_allow_##TAG<MINB_S, mrg::K_SCALAR>() | mrg_allow_##TAG<MINB_R, mrg::K_RECOLL>(); \
+                 mrg_allow_##TAG<MINB_S, mrg::K_SCALAR>() | mrg_allow_##TAG<MINB_R, mrg::K_RECOLL>() | \
+                 mrg_allow_##TAG<MINB, mrg::K_LARGE>();                                           \
         if (!rc && dev >= 0 && dev < 64) done[dev].store(1, std::memory_order_release);            \
         return rc;                                                                                \
     }                                                                                             \
@@ -2093,12 +2378,13 @@ __global__ void __launch_bounds__(NT, MINB) mr_persistent(LaunchArgs a) {
     int mrg_launch_##TAG(int grid, const mrg::LaunchArgs &a, cudaStream_t s, int prio) {           \
         int rc = mrg_attr_##TAG();                                                                \
         if (rc) return rc;                                                                        \
-        const size_t dyn = mrg_dyn_##TAG(a.smem_mask_words);                                       \
+        const size_t dyn = mrg_dyn_##TAG(a.smem_mask_words + a.smem_list_words);                   \
         switch (a.kind) {                                                                         \
         case mrg::K_FAST: return mrg_go_##TAG<MINB, mrg::K_FAST>(grid, a, dyn, s, prio);           \
         case mrg::K_GENERAL: return mrg_go_##TAG<MINB_G, mrg::K_GENERAL>(grid, a, dyn, s, prio);   \
         case mrg::K_SCALAR: return mrg_go_##TAG<MINB_S, mrg::K_SCALAR>(grid, a, dyn, s, prio);     \
         case mrg::K_RECOLL: return mrg_go_##TAG<MINB_R, mrg::K_RECOLL>(grid, a, dyn, s, prio);     \
+        case mrg::K_LARGE: return mrg_go_##TAG<MINB, mrg::K_LARGE>(grid, a, dyn, s, prio);         \
         }                                                                                         \
         return (int)cudaErrorInvalidValue;                                                        \
     }                                                                                             \
@@ -2111,6 +2397,7 @@ __global__ void __launch_bounds__(NT, MINB) mr_persistent(LaunchArgs a) {
         case mrg::K_GENERAL: return mrg_occ1_##TAG<MINB_G, mrg::K_GENERAL>(dyn, nb);               \
         case mrg::K_SCALAR: return mrg_occ1_##TAG<MINB_S, mrg::K_SCALAR>(dyn, nb);                 \
         case mrg::K_RECOLL: return mrg_occ1_##TAG<MINB_R, mrg::K_RECOLL>(dyn, nb);                   \
+        case mrg::K_LARGE: return mrg_occ1_##TAG<MINB, mrg::K_LARGE>(dyn, nb);                     \
         }                                                                                         \
         return (int)cudaErrorInvalidValue;                                                        \
     }                                                                                             \

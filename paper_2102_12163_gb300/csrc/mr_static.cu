@@ -105,8 +105,12 @@ extern "C" mr_status mr_run_static(const mr_instance_desc *desc, int precision, 
     // layout of the scratch area for this instance (same regions as a bound context)
     const int q = mrg_npop(d.eq);
     const long long S = (1LL << (d.Jmax + 1)) - (1LL << d.Jmin), N = 1LL << d.Jmax;
-    int W = 0;
-    for (int l = d.Jmin; l <= d.Jmax; ++l) W += l >= 5 ? (1 << (l - 5)) : 1;
+    int W = 0, OW = 0;
+    for (int l = d.Jmin; l <= d.Jmax; ++l) {
+        W += l >= 5 ? (1 << (l - 5)) : 1;
+        OW += occ_words_of(l);
+    }
+    const long long region = mask_region_words(W, OW);
     const size_t vb = fp32 ? 4 : 8;
     size_t o = 0;
     const size_t oDesc = o;
@@ -122,7 +126,7 @@ extern "C" mr_status mr_run_static(const mr_instance_desc *desc, int precision, 
     const size_t oPhi = o;
     o = align256(o + vb * q * (N + 1));
     const size_t oM = o;
-    o = align256(o + sizeof(uint32_t) * NMASK * W);
+    o = align256(o + sizeof(uint32_t) * (size_t)region);
     const size_t oL = o;
     long long lo = 0, list_off[NLIST];
     for (int L = 0; L < NLIST; ++L) {
@@ -163,6 +167,7 @@ extern "C" mr_status mr_run_static(const mr_instance_desc *desc, int precision, 
         if (fr == 0.5 && e2 - 1 >= -16 && e2 - 1 <= 16) h.lam_log2 = e2 - 1;
     }
     h.Wtot = W;
+    h.OW = OW;
     h.eps = d.eps;
     h.a = d.a;
     h.b = d.b;
@@ -196,7 +201,7 @@ extern "C" mr_status mr_run_static(const mr_instance_desc *desc, int precision, 
     // one block for the instance, bitmasks in shared memory when they fit
     const int block = d.Jmax >= 12 ? 1024 : 512;
     size_t sbase = mrg_smem_bytes(fp32, block, 0), limit = 220u * 1024u;
-    int fit = limit > sbase ? (int)((limit - sbase) / (NMASK * sizeof(uint32_t))) : 0;
+    long long fit = limit > sbase ? (long long)((limit - sbase) / sizeof(uint32_t)) : 0;
     LaunchArgs a;
     std::memset(&a, 0, sizeof a);
     a.descs = (const InstDesc *)(base + oDesc);
@@ -204,8 +209,13 @@ extern "C" mr_status mr_run_static(const mr_instance_desc *desc, int precision, 
     a.n = 1;
     a.queue = (int *)(base + oQueue);
     a.tables = base + oTab + (fp32 ? sizeof(Tables<double>) : 0);
-    a.smem_mask_words = W <= fit ? W : 0;
-    a.kind = d.gamma > 1 ? K_GENERAL : d.collision != 0 ? K_RECOLL : K_FAST;
+    const long long sregion = smem_region_words(W, OW);
+    a.smem_mask_words = sregion <= fit ? (int)sregion : 0;
+    // the rest of the shared memory holds the first entries of the cell lists
+    long long lw = fit - a.smem_mask_words;
+    lw = lw < NLIST * 256LL ? lw : NLIST * 256LL;
+    a.smem_list_words = lw > 0 ? (int)(lw / NLIST * NLIST) : 0;
+    a.kind = d.gamma > 1 ? K_GENERAL : d.collision != 0 ? K_RECOLL : W >= CW_MIN_WORDS ? K_LARGE : K_FAST;
     const int phases[3] = {PH_INIT_FULL, PH_ADAPT | PH_STEP, PH_FINEST};
     const int steps[3] = {0, nsteps, 0};
     for (int i = 0; i < 3; ++i) {
