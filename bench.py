@@ -390,16 +390,21 @@ def singles(latency):
             dt = e0.elapsed_time(e1) / 1e3
             u1, _, _ = s.stats()
             st1, ps1 = s.step_passes()
-            passes = (ps1 - ps0) / max(1, st1 - st0)
-            floor_us = passes * latency["global_handover_cycles"] / sm_max
+            # the kernel variants of the large instances count their barriers; the batch
+            # variants (Jmax < 15 here) do not (it cost them 7 %), so these get no floor
+            passes = (ps1 - ps0) / max(1, st1 - st0) if ps1 > ps0 else None
+            floor_us = passes * latency["global_handover_cycles"] / sm_max if passes else None
             row[key] = {"us_per_step": dt / K * 1e6, "updates_per_s": (u1 - u0) / dt,
                         "leaves_per_step": (u1 - u0) / K, "passes_per_step": passes,
-                        "floor_us_per_step": floor_us, "step_over_floor": dt / K * 1e6 / floor_us}
+                        "floor_us_per_step": floor_us,
+                        "step_over_floor": dt / K * 1e6 / floor_us if floor_us else None}
             s.close()
         out[name] = row
     out["floor_model"] = {"handover": latency, "sm_clock_mhz": sm_max,
                           "meaning": "passes per step x one warp-to-warp hand-over through global memory and a "
-                                     "block barrier (mr_probe_latency), at the maximum SM clock"}
+                                     "block barrier (mr_probe_latency), at the maximum SM clock; passes are counted "
+                                     "by the kernel variant of instances with >= 2048 mask words per bitmask "
+                                     "(Jmax >= 15), null for the others"}
     return out
 
 

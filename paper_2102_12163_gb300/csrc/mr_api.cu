@@ -91,11 +91,6 @@ int kind_of(const InstDesc &h) {
 
 thread_local std::string g_create_error;
 
-// shared-memory entries per cell list at most: shared memory is carved out of
-// the SM's L1, which keeps the population values of the resident instances
-// between passes; on the Jmax 8..14 batch 256 entries per list ran 2 % faster
-// than none, 1024 and 4096 entries 4 % and 7 % slower (one box)
-constexpr int kListEntries = 256;
 
 // Latency probe: warps 0 and 1 of one block alternately read the value the
 // other wrote and write the next one, with a block barrier after every
@@ -159,7 +154,6 @@ struct mr_ctx {
     int block = 0, grid_req = 0, sms = 0;
     int grid[NKIND] = {};      // blocks per launch, by kernel variant (K_*)
     int mask_cap[NKIND] = {};  // mask-region words a block team keeps in shared memory, by variant
-    int list_cap[NKIND] = {};  // shared-memory words for the first entries of the cell lists, by variant
     int wmax = 0;              // mask-region words of the largest instance
     int n_group[NGROUP] = {};  // instances per group of the queue order (group_of)
     int group_kind[NGROUP] = {K_GENERAL, K_RECOLL, K_LARGE, K_FAST};  // kernel variant of each group
@@ -383,7 +377,6 @@ static int launch_group(mr_ctx *c, int phases, int nsteps, const int *order, int
     a.aux1 = aux1;
     a.tables = c->ws + c->off_tab + (c->fp32() ? sizeof(Tables<double>) : 0);
     a.smem_mask_words = c->mask_cap[kind];
-    a.smem_list_words = c->list_cap[kind];
     int rc = c->cuda(cudaMemsetAsync(a.queue, 0, sizeof(int), stream), "cudaMemsetAsync");
     if (rc) return rc;
     int grid = std::min(a.n, c->grid[kind]);
@@ -562,16 +555,14 @@ static int configure(mr_ctx *c) {
         size_t budget = c->n() == 1 ? 220u * 1024u : (227u * 1024u) / (size_t)minb - 1024u;
         int fit = budget > base ? (int)((budget - base) / sizeof(uint32_t)) : 0;
         // the mask region of the largest instance when it fits (a batch keeps the
-        // area for the instances that fit; a lone instance that does not fit
-        // leaves it empty); the rest holds the first entries of the cell lists
+        // area for the instances that fit); a lone instance that does not fit
+        // leaves it empty: shared memory is carved out of the SM's L1, which
+        // keeps the population values between passes
         int mc = std::min(c->wmax, fit);
         if (c->n() == 1 && c->wmax > fit) mc = 0;
-        int lw = std::min(fit - mc, NLIST * kListEntries);
-        lw = std::max(0, lw / NLIST * NLIST);
         c->mask_cap[kind] = mc;
-        c->list_cap[kind] = lw;
         int nb = 0;
-        int rc = c->cuda((cudaError_t)mrg_occupancy(c->fp32(), c->block, kind, mc + lw, &nb), "occupancy");
+        int rc = c->cuda((cudaError_t)mrg_occupancy(c->fp32(), c->block, kind, mc, &nb), "occupancy");
         if (rc) return rc;
         c->grid[kind] = c->grid_req > 0 ? c->grid_req : std::max(1, nb) * c->sms;
     }
@@ -807,7 +798,7 @@ mr_status mr_get_leaves(mr_ctx *c, int inst, int *level, long *index, double *f,
         if (index) index[i] = k;
         if (f) {
             long long cell = ((1LL << l) - (1LL << h.Jmin)) + k;
-            for (int hh = 0; hh < q; ++hh) f[(long)hh * cap + i] = vals[(size_t)hh * h.S + cell];
+            for (int hh = 0; hh < q; ++hh) f[(long)hh * cap + i] = vals[(size_t)cell * q + hh];
         }
     }
     return MR_OK;
@@ -832,7 +823,7 @@ mr_status mr_get_moments(mr_ctx *c, int inst, double *m, long cap, long *count) 
                 const double w[5] = {0.0, 1.0, -1.0, 2.0, -2.0};
                 double m0 = 0.0, m1 = 0.0;
                 for (int hh = 0; hh < npop_of(h.eq); ++hh) {
-                    const double f = vals[(size_t)hh * h.S + cell];
+                    const double f = vals[(size_t)cell * npop_of(h.eq) + hh];
                     m0 += f;
                     m1 += (w[hh] * h.lam) * f;
                 }
@@ -840,7 +831,7 @@ mr_status mr_get_moments(mr_ctx *c, int inst, double *m, long cap, long *count) 
                 m[(long)cap + i] = m1;
             } else {
                 for (int j = 0; j < h.nf; ++j)
-                    m[(long)j * cap + i] = vals[(size_t)(2 * j) * h.S + cell] + vals[(size_t)(2 * j + 1) * h.S + cell];
+                    m[(long)j * cap + i] = vals[(size_t)cell * npop_of(h.eq) + 2 * j] + vals[(size_t)cell * npop_of(h.eq) + 2 * j + 1];
             }
         }
     return MR_OK;

@@ -2,11 +2,11 @@
 // the C ABI (include/mrlbm.h).  Internal to the library.
 //
 // Per instance the device workspace holds (all 256-byte aligned):
-//   V      q x S values, population-major, level l at cells [2^l - 2^Jmin, ...)
-//          (dense level-wise arrays: every cell of every level has a slot)
-//   Phi    q x (2^Jmax + 1) reconstructed boundary values, indexed by the
-//          finest-lattice interface they belong to; also the staging area of
-//          the initial data
+//   V      S x q values, cell-major (the q populations of a cell contiguous),
+//          level l at cells [2^l - 2^Jmin, ...) (dense level-wise arrays:
+//          every cell of every level has a slot)
+//   Phi    (2^Jmax + 1) x q reconstructed boundary values, interface-major,
+//          indexed by the finest-lattice interface they belong to
 //   masks  NMASK bitmasks over all cells of all levels, 32 cells per word,
 //          level l at words [woff_l, woff_l + max(1, 2^l / 32)); then the
 //          candidate-word list of the step (Wtot entries at most) and two
@@ -40,8 +40,9 @@ enum { L_INT = 0, L_LEAF = 1, L_PRED = 2, L_GH = 3, NLIST = 4 };
 enum { PH_INIT_FULL = 1, PH_INIT_STATE = 2, PH_ADAPT = 4, PH_STEP = 8, PH_FINEST = 16 };
 // device status bits
 // ST_FLUXED: the last step streamed with interface values in Phi (D1Q2^n
-// schemes) and left the internal cells holding the projection of f*, so the
-// next projection of the leaves is one conservative update (see the kernel).
+// schemes) and, in the same pass, moved every internal cell by the flux through
+// its own edges, so the internal cells hold the projection of the leaves and the
+// next adaptation skips its projection (see the kernel).
 enum { ST_NONFINITE = 1, ST_FLUXED = 2 };
 // phases timed by the profiling build (MRG_PHASE_TIMERS)
 enum {
@@ -89,11 +90,10 @@ struct InstDesc {
     // correctly rounded reciprocal of lambda, for the FP64 division by lambda
     // with one correction step (see the kernel's div_lam)
     double rlam;
-    // constant factors of the collision, rounded once in the path's precision
-    // exactly as the per-cell expressions would round them: 1 - s[j]; Euler
-    // 1.5 - 0.5 gamma_gas, gamma_gas - 1, 0.5 (1 - gamma_gas); shallow water 0.5 g
+    // constant factors of the FP64 collision, rounded once exactly as the
+    // per-cell expressions would round them: 1 - s[j]; Euler 1.5 - 0.5 gamma_gas,
+    // gamma_gas - 1, 0.5 (1 - gamma_gas); shallow water 0.5 g
     double oms[3], eu_a, eu_b, eu_c, sw_g2;
-    float oms_f[3], eu_a_f, eu_b_f, eu_c_f, sw_g2_f;
 };
 
 // words of the mask region of an instance: NMASK bitmasks, the candidate-word
@@ -123,18 +123,11 @@ inline void fill_float_constants(InstDesc &h) {
     for (int i = 0; i < 5; ++i)
         for (int j = 0; j < 5; ++j) h.minv_f[i][j] = (float)h.minv[i][j];
     h.rlam = 1.0 / h.lam;  // IEEE division: correctly rounded
-    for (int j = 0; j < 3; ++j) {
-        h.oms[j] = 1.0 - h.s[j];
-        h.oms_f[j] = 1.0f - h.s_f[j];
-    }
+    for (int j = 0; j < 3; ++j) h.oms[j] = 1.0 - h.s[j];
     h.eu_a = 1.5 - 0.5 * h.eqp;
     h.eu_b = h.eqp - 1.0;
     h.eu_c = 0.5 * (1.0 - h.eqp);
     h.sw_g2 = 0.5 * h.eqp;
-    h.eu_a_f = 1.5f - 0.5f * h.eqp_f;
-    h.eu_b_f = h.eqp_f - 1.0f;
-    h.eu_c_f = 0.5f * (1.0f - h.eqp_f);
-    h.sw_g2_f = 0.5f * h.eqp_f;
 }
 
 // Reconstruction tables for gamma = 1, indexed by the level gap dj = Jmax - l
@@ -169,7 +162,6 @@ struct LaunchArgs {
     const void *aux1;
     const void *tables;   // Tables<T> in device memory
     int smem_mask_words;  // block teams keep their mask region in shared memory when it has at most this many words
-    int smem_list_words;  // shared-memory words after the mask area holding the first entries of the NLIST cell lists
     int kind;             // kernel variant (K_*) the launch runs
 };
 

@@ -256,17 +256,23 @@ template <typename T>
 __device__ __forceinline__ T minv_of(const InstDesc &d, int h, int i) {
     if constexpr (sizeof(T) == 8) return d.minv[h][i]; else return d.minv_f[h][i];
 }
-// 1 - s[i] and the equilibria's constant factors, rounded once on the host
+// 1 - s[i] and the equilibria's constant factors: in FP64 rounded once on the
+// host (GB300's FP64 pipe is the scarce one), in FP32 computed in place (the
+// loads cost the FP32 kernel registers, the operations cost it nothing)
 template <typename T>
 __device__ __forceinline__ T oms_of(const InstDesc &d, int i) {
-    if constexpr (sizeof(T) == 8) return d.oms[i]; else return d.oms_f[i];
+    if constexpr (sizeof(T) == 8) return d.oms[i]; else return 1.0f - d.s_f[i];
 }
 template <typename T>
 __device__ __forceinline__ void eq_consts(const InstDesc &d, T &a, T &b, T &c, T &g2) {
     if constexpr (sizeof(T) == 8) {
         a = d.eu_a; b = d.eu_b; c = d.eu_c; g2 = d.sw_g2;
     } else {
-        a = d.eu_a_f; b = d.eu_b_f; c = d.eu_c_f; g2 = d.sw_g2_f;
+        const float gg = d.eqp_f;
+        a = 1.5f - 0.5f * gg;
+        b = gg - 1.0f;
+        c = 0.5f * (1.0f - gg);
+        g2 = 0.5f * gg;
     }
 }
 
@@ -417,8 +423,8 @@ __device__ __forceinline__ void dq_equilibrium_populations(const InstDesc &d, co
 }
 
 // prediction of child `odd` of cell p of a row at level lp (Section 3.1, gamma = 1)
-template <typename T>
-__device__ __forceinline__ T predict(const T *row, long long p, int odd, int lp, int bc) {
+template <typename T, typename R>
+__device__ __forceinline__ T predict(const R &row, long long p, int odd, int lp, int bc) {
     T vl = row[wrapc(p - 1, lp, bc)], vp = row[p], vr = row[wrapc(p + 1, lp, bc)];
     T t = T(C1) * (vr - vl);  // exact: c_1 is a power of two
     return odd ? vp - t : vp + t;
@@ -426,8 +432,8 @@ __device__ __forceinline__ T predict(const T *row, long long p, int odd, int lp,
 
 // the same for a stencil of half-width gamma = 2 or 3 (coefficients c[0..gamma-1]):
 // f_p +- sum_a c_a (f_{p+a} - f_{p-a}), the sum accumulated in increasing a
-template <typename T>
-__device__ __forceinline__ T predict_g(const T *row, long long p, int odd, int lp, int bc, int gamma, const T *c) {
+template <typename T, typename R>
+__device__ __forceinline__ T predict_g(const R &row, long long p, int odd, int lp, int bc, int gamma, const T *c) {
     T t = c[0] * (row[wrapc(p + 1, lp, bc)] - row[wrapc(p - 1, lp, bc)]);
 #pragma unroll
     for (int a = 2; a <= 3; ++a)
@@ -457,19 +463,19 @@ __device__ __forceinline__ uint32_t fold3(uint32_t t) {
 // its value is used instead.  Out-of-domain cells take the value of the nearest
 // domain cell (copy boundary) or wrap (periodic), as in the prediction.
 template <typename T, int G, bool LAST>
-__device__ __noinline__ T edge_walk(const T *rowbase, int Jmin, int Jmax, int bc, const uint32_t *R, const int *woff,
-                                    const T *c, int l, long long k) {
+__device__ __noinline__ T edge_walk(const T *rowbase, int qs, int Jmin, int Jmax, int bc, const uint32_t *R,
+                                    const int *woff, const T *c, int l, long long k) {
     constexpr int W = 4 * G + 1, C = 2 * G, E = LAST ? 1 : 0;
     T w[W], nw[W];
     {
-        const T *row = rowbase + cell_off(l, Jmin);
+        const T *row = rowbase + cell_off(l, Jmin) * qs;
 #pragma unroll
-        for (int t = 0; t < W; ++t) w[t] = row[wrapc(k + t - C, l, bc)];
+        for (int t = 0; t < W; ++t) w[t] = row[wrapc(k + t - C, l, bc) * qs];
     }
     long long i = k;
     for (int m = l; m < Jmax; ++m) {
         const long long nn = 1LL << (m + 1), inext = 2 * i + E;
-        const T *row = rowbase + cell_off(m + 1, Jmin);
+        const T *row = rowbase + cell_off(m + 1, Jmin) * qs;
         const uint32_t *Rm = R + woff[m + 1];
         T lo = T(0), hi = T(0);  // values of the first and last cells of the level (copy boundary)
 #pragma unroll
@@ -486,7 +492,7 @@ __device__ __noinline__ T edge_walk(const T *rowbase, int Jmin, int Jmax, int bc
                 inside = pos >= 0 && pos < nn;
             T v;
             if (inside && ((Rm[(int)(cp >> 5)] >> (cp & 31)) & 1u)) {
-                v = row[cp];
+                v = row[cp * qs];
             } else {
                 T sum = c[0] * (w[pp + 1] - w[pp - 1]);
 #pragma unroll
@@ -545,26 +551,17 @@ __device__ __forceinline__ void decide_bits(unsigned long long Db, double el, do
 }
 
 // ---------------------------------------------------------------------------
-// A compacted cell list: its first `cap` entries in shared memory (written and
-// read within the block at shared-memory latency), the rest in global memory
-// at the same positions.
-struct ListView {
-    uint32_t *s;  // shared-memory part
-    uint32_t *g;  // global list (all positions)
-    int cap;
-    __device__ __forceinline__ uint32_t operator[](int i) const { return i < cap ? s[i] : g[i]; }
-    __device__ __forceinline__ void put(int i, uint32_t v) const {
-        if (i < cap)
-            s[i] = v;
-        else
-            g[i] = v;
-    }
-};
-
-// ---------------------------------------------------------------------------
 // the instance worker; TS threads (a warp or the whole block) form the team
 
 constexpr int QMAX = 6;  // populations of the largest scheme (vectorial D1Q2^3)
+
+// One population of the cell-major value layout: the Q values of a cell are
+// contiguous, so element k of the population starting at p sits at p[k * Q].
+template <typename T, int Q>
+struct SRow {
+    T *p;
+    __device__ __forceinline__ T &operator[](long long k) const { return p[k * Q]; }
+};
 
 // WIDE: prediction stencils gamma = 2, 3 (the gamma = 1 code is a separate instantiation)
 // SPM: word passes over candidate words never (0), for the instances with at
@@ -584,19 +581,13 @@ struct Worker {
     T *V;
     T *Phi;
     uint32_t *M;  // mask base (shared memory when the masks fit, else global)
-    uint32_t *SL; // shared-memory parts of the cell lists (lcap entries each)
-    int lcap;
     int tid;      // rank in the team
-    mutable unsigned npass = 0;  // team barriers of this launch (added to the instance's count at its end)
 
-    __device__ Worker(TeamSmem<T> &s, const Tables<T> &tb, BlockScratch &x, int rank, uint32_t *masks, uint32_t *slist,
-                      int list_cap)
+    __device__ Worker(TeamSmem<T> &s, const Tables<T> &tb, BlockScratch &x, int rank, uint32_t *masks)
         : sm(s), tab(tb), bx(x), d(s.d), tid(rank) {
         V = (T *)d.V;
         Phi = (T *)d.Phi;
         M = masks;
-        SL = slist;
-        lcap = slist ? list_cap : 0;
     }
 
     // leaves collision of the q populations of one cell
@@ -607,14 +598,18 @@ struct Worker {
             collide<T, NF>(d, f);
     }
 
-    // team barrier; every one ends a pass whose results the next pass reads
-    // (counted, so a step's chain of dependent passes can be measured)
+    // team barrier; every one ends a pass whose results the next pass reads.
+    // The variants that run large single instances count them (the chain of
+    // dependent passes of a step, the floor of its latency) by the team's last
+    // thread after the barrier; the batch variants do not: the count cost them
+    // 7 % (measured), most of their passes being short.
     __device__ __forceinline__ void sync() const {
-        ++npass;
         if constexpr (WARP)
             __syncwarp();
         else
             __syncthreads();
+        if constexpr (SPM != 0)
+            if (tid == TS - 1) ++sm.passes;
     }
 
     // profiling build: cycles since the previous tick charged to phase p (after a team barrier)
@@ -647,10 +642,10 @@ struct Worker {
     // occupancy bitmap of tree buffer b (M_R0 or M_R1): bit wi & 31 of word ooff[l] + (wi >> 5) is set
     // when word wi of level l of that tree holds a cell
     __device__ __forceinline__ uint32_t *occ(int b) { return M + (long long)(NMASK + 1) * d.Wtot + (long long)b * d.OW; }
-    __device__ __forceinline__ ListView list(int L) {
-        return ListView{SL + (long long)L * lcap, d.lists + d.list_off[L], lcap};
-    }
-    __device__ __forceinline__ T *row(int h, int l) { return V + (long long)h * d.S + cell_off(l, d.Jmin); }
+    __device__ __forceinline__ uint32_t *list(int L) { return d.lists + d.list_off[L]; }
+    // population h on level l, and population h of the interface array
+    __device__ __forceinline__ SRow<T, q> row(int h, int l) const { return SRow<T, q>{V + cell_off(l, d.Jmin) * q + h}; }
+    __device__ __forceinline__ SRow<T, q> phi(int h) const { return SRow<T, q>{Phi + h}; }
 
     // sums over the team of nf per-thread doubles, valid in thread 0 (one barrier)
     __device__ __forceinline__ void team_sum(double (&x)[3]) {
@@ -724,23 +719,28 @@ struct Worker {
     }
 
     // ---- projection of the internal cells of level l (Def. Projection operator)
-    __device__ __forceinline__ void project_level(const ListView &lst, int l) {
+    __device__ __forceinline__ void project_level(const uint32_t *lst, int l) {
         int b = sm.seg[L_INT][l], e = sm.seg[L_INT][l + 1];
         for (int i = b + tid; i < e; i += TS) {
             long long k = lst[i] & KMASK;
-            typename V2<T>::type c[QMAX];
+            // the two children are adjacent cells: 2q contiguous values
+            T ce[QMAX], co[QMAX];
 #pragma unroll
             for (int h = 0; h < QMAX; ++h)
-                if (h < q) c[h] = *reinterpret_cast<const typename V2<T>::type *>(row(h, l + 1) + 2 * k);
+                if (h < q) {
+                    const auto rc = row(h, l + 1);
+                    ce[h] = rc[2 * k];
+                    co[h] = rc[2 * k + 1];
+                }
 #pragma unroll
             for (int h = 0; h < QMAX; ++h)
-                if (h < q) row(h, l)[k] = half_of<T>(c[h].x + c[h].y);
+                if (h < q) row(h, l)[k] = half_of<T>(ce[h] + co[h]);
         }
     }
 
     // ---- S1: leaves collision (eq. LeavesCollision) ---------------------------
     __device__ void collide_all() {
-        const ListView lst = list(L_LEAF);
+        const uint32_t *lst = list(L_LEAF);
         for (int i = tid; i < sm.nleaf; i += TS) {
             uint32_t ent = lst[i];
             int l = ent >> KBITS;
@@ -805,7 +805,7 @@ struct Worker {
         constexpr int NR = DQ ? q - 2 : nf;  // relaxed moments
         constexpr int NWARP = TS / 32;
         const int lane = tid & 31, warp = tid >> 5;
-        const ListView leaves = list(L_LEAF);
+        const uint32_t *leaves = list(L_LEAF);
         const long long stride = d.N + 1;
         for (int i = warp; i < sm.nleaf; i += NWARP) {
             const uint32_t ent = leaves[i];
@@ -889,7 +889,7 @@ struct Worker {
 
     // ---- A1 / S2: projection sweep, fine to coarse ---------------------------
     __device__ void upsweep() {
-        const ListView li = list(L_INT);
+        const uint32_t *li = list(L_INT);
         for (int l = d.Jmax - 1; l >= d.Jmin; --l) {
             if (sm.seg[L_INT][l] == sm.seg[L_INT][l + 1]) continue;
             project_level(li, l);
@@ -906,8 +906,11 @@ struct Worker {
     // the tree).  One update of every internal cell, all levels in one pass,
     // therefore equals the level-by-level projection of the streamed leaves up
     // to rounding, and replaces its Jmax - Jmin dependent passes.
-    __device__ void project_by_flux() {
-        const ListView li = list(L_INT);
+    // The update runs in the stream's own pass (S5): it reads only Phi, which S4
+    // completed, and the internal cells, which S5 does not touch; the next
+    // adaptation then starts from projected internal cells (status ST_FLUXED).
+    __device__ __forceinline__ void project_by_flux_pass() {
+        const uint32_t *li = list(L_INT);
         const int b = sm.seg[L_INT][d.Jmin], e = sm.seg[L_INT][d.Jmax];
         for (int i = b + tid; i < e; i += TS) {
             const uint32_t ent = li[i];
@@ -920,13 +923,12 @@ struct Worker {
 #pragma unroll
             for (int h = 0; h < QMAX; ++h)
                 if (h < q) {
-                    const T *ph = Phi + (long long)h * (d.N + 1);
+                    const auto ph = phi(h);
                     const T coef = (h & 1) ? -w : w;
-                    T *r = row(h, l);
+                    const auto r = row(h, l);
                     r[k] = r[k] + coef * (ph[first] - ph[next]);
                 }
         }
-        sync();
     }
 
     // ---- A2: details of the pairs of the tree, threshold T, Harten flags ----
@@ -940,7 +942,7 @@ struct Worker {
             return;
         }
         // the even cells of the tree above Jmin: first children 2p of the internal cells p
-        const ListView lst = list(L_INT);
+        const uint32_t *lst = list(L_INT);
         int b = sm.seg[L_INT][d.Jmin], e = sm.seg[L_INT][d.Jmax];
         uint32_t *keep = mask(M_KEEP), *ref = mask(M_REF);
         for (int i = b + tid; i < e; i += TS) {
@@ -955,7 +957,7 @@ struct Worker {
 #pragma unroll
                 for (int h = 0; h < QMAX; ++h)
                     if (h < q) {
-                        const T *rc = row(h, l - 1);
+                        const auto rc = row(h, l - 1);
                         const double dv = row(h, l)[k] - (rc[p] + C1 * (rc[pr] - rc[pl]));
                         const unsigned long long b = abs_bits(dv);
                         Db = b > Db ? b : Db;
@@ -966,7 +968,7 @@ struct Worker {
 #pragma unroll
                 for (int h = 0; h < QMAX; ++h)
                     if (h < q) {
-                        const T *rc = row(h, l - 1);
+                        const auto rc = row(h, l - 1);
                         float vk = row(h, l)[k], vl = rc[pl], vp = rc[p], vr = rc[pr];
                         float dv = vk - (vp + float(C1) * (vr - vl));
                         D = fmaxf(D, fabsf(dv));
@@ -979,7 +981,7 @@ struct Worker {
                 if (amb) {
                     double Dd = 0.0;
                     for (int h = 0; h < q; ++h) {
-                        const T *rc = row(h, l - 1);
+                        const auto rc = row(h, l - 1);
                         double dv = (double)row(h, l)[k] - ((double)rc[p] + C1 * ((double)rc[pr] - (double)rc[pl]));
                         Dd = fmax(Dd, fabs(dv));
                     }
@@ -1007,7 +1009,7 @@ struct Worker {
     // the number of operations, (6 gamma + 2) u times the sum of |inputs|
     // (3 gamma + 1 roundings, each at most u times that sum, with a factor 2 margin)
     __device__ __noinline__ void details_wide() {
-        const ListView lst = list(L_INT);  // first children 2p of the internal cells p
+        const uint32_t *lst = list(L_INT);  // first children 2p of the internal cells p
         const int b = sm.seg[L_INT][d.Jmin], e = sm.seg[L_INT][d.Jmax], g = d.gamma;
         const T *c = tab.pc[g];
         uint32_t *keep = mask(M_KEEP), *ref = mask(M_REF);
@@ -1021,7 +1023,7 @@ struct Worker {
             unsigned long long Db = 0ull;
             float Df = 0.0f, B = 0.0f;
             for (int h = 0; h < q; ++h) {
-                const T *rc = row(h, l - 1);
+                const auto rc = row(h, l - 1);
                 T sum = T(0);
                 float mag = 0.0f;
                 for (int a = 1; a <= g; ++a) {
@@ -1046,7 +1048,7 @@ struct Worker {
                 const bool amb = fabsf(Df - el) <= B + el * 0x1p-22f || (hasref && fabsf(Df - bl) <= B + bl * 0x1p-22f);
                 if (amb) {
                     for (int h = 0; h < q; ++h) {
-                        const T *rc = row(h, l - 1);
+                        const auto rc = row(h, l - 1);
                         double sum = 0.0;
                         for (int a = 1; a <= g; ++a)
                             sum = a == 1 ? (double)c[0] * ((double)rc[wrapc(p + 1, l - 1, d.bc)] - (double)rc[wrapc(p - 1, l - 1, d.bc)])
@@ -1421,11 +1423,11 @@ struct Worker {
                     sm.seg[L][l] = off;
                     for (int k = l - 1; k >= d.Jmin && sm.cw_seg[k] == sm.cw_seg[l]; --k) sm.seg[L][k] = off;
                 }
-                const ListView dst = list(L);
+                uint32_t *dst = list(L);
                 while (x) {
                     const int bit = __ffs(x) - 1;
                     x &= x - 1u;
-                    dst.put(off++, pk + (uint32_t)bit);
+                    dst[off++] = pk + (uint32_t)bit;
                 }
                 run[L] += tot;
             }
@@ -1437,6 +1439,168 @@ struct Worker {
             for (int k = d.Jmax; k >= d.Jmin && sm.cw_seg[k] == ncw; --k)
 #pragma unroll
                 for (int L = 0; L < NLIST; ++L) sm.seg[L][k] = run[L];
+            sm.nleaf = run[L_LEAF];
+        }
+        sync();
+    }
+
+    // ---- the word passes over every word (instances without candidate words) ----
+    __device__ void enlarge_dense(uint32_t *Rn) {
+        const uint32_t *keep = mask(M_KEEP), *ref = mask(M_REF);
+        for (int g = tid; g < d.Wtot; g += TS) {
+            int l, wi;
+            level_of_word(sm, g, l, wi);
+            uint32_t vb = valid_bits(l), rh;
+            if (l == d.Jmin) {
+                rh = vb;
+            } else {
+                const uint32_t *kl = keep + sm.woff[l];
+                uint32_t rt = kl[wi];
+                rh = rt | pairexpand(dilate([&](int j) { return kl[j]; }, l, wi, SIGMA, d.bc));
+                if (l >= d.Jmin + 2) rh |= spread16(ref[sm.woff[l - 1] + (wi >> 1)] >> (16 * (wi & 1)));
+            }
+            Rn[g] = rh & vb;
+        }
+    }
+
+    __device__ void grade_and_mark_dense(uint32_t *Rn, const uint32_t *Ro, bool grade) {
+        uint32_t *LF = mask(M_LEAF), *PR = mask(M_PRED), *GH = mask(M_GH);
+        const int g = d.gamma;
+        const int lbig = d.Jmin > 6 ? d.Jmin : 6;
+        for (int l = d.Jmax; l >= lbig; --l) {
+            const int Wl = 1 << (l - 5);
+            const uint32_t *rl = Rn + sm.woff[l];
+            if (grade && l > d.Jmin + 1) {
+                uint32_t *rp = Rn + sm.woff[l - 1];
+                if constexpr (!WIDE) {
+                    for (int wp = tid; wp < (Wl >> 1); wp += TS) {
+                        uint32_t x = fold2(rl[2 * wp], rl[2 * wp + 1]);
+                        bool eL = (word_bc(rl, 2 * wp - 1, Wl, d.bc) >> 30) != 0u;  // children of parent 32 wp - 1
+                        bool eR = (word_bc(rl, 2 * wp + 2, Wl, d.bc) & 3u) != 0u;   // children of parent 32 wp + 32
+                        rp[wp] |= pairexpand(dilate1_edges(x, eL, eR));
+                    }
+                } else {
+                    for (int wp = tid; wp < (Wl >> 1); wp += TS) {
+                        const uint32_t x = fold2(rl[2 * wp], rl[2 * wp + 1]);
+                        // parents 29..31 of the word on the left, 0..2 of the word on the right
+                        const uint32_t xl = fold3(word_bc(rl, 2 * wp - 1, Wl, d.bc) >> 26) << 29;
+                        const uint32_t xr = fold3(word_bc(rl, 2 * wp + 2, Wl, d.bc) & 63u);
+                        rp[wp] |= pairexpand(dilate_edges(x, xl, xr, g));
+                    }
+                }
+            }
+            const uint32_t *rol = Ro + sm.woff[l];
+            uint32_t *lfl = LF + sm.woff[l], *prl = PR + sm.woff[l], *ghl = GH + sm.woff[l];
+            if (l == d.Jmax) {
+                for (int wi = tid; wi < Wl; wi += TS) {
+                    uint32_t r = rl[wi];
+                    lfl[wi] = r;
+                    prl[wi] = r & ~rol[wi];
+                    ghl[wi] = 0u;
+                }
+            } else if constexpr (WIDE) {
+                const int Wc = Wl << 1;
+                const uint32_t *rc = Rn + sm.woff[l + 1], *pc = PR + sm.woff[l + 1], *gc = GH + sm.woff[l + 1];
+                for (int wi = tid; wi < Wl; wi += TS) {
+                    const uint32_t r = rl[wi], ro = rol[wi];
+                    const uint32_t lf = r & ~fold2(rc[2 * wi], rc[2 * wi + 1]);
+                    // leaf bits of the 16 cells of each neighbouring word next to this one
+                    const uint32_t cL = word_bc(rc, 2 * wi - 1, Wc, d.bc), cR = word_bc(rc, 2 * wi + 2, Wc, d.bc);
+                    const uint32_t lfL = word_bc(rl, wi - 1, Wl, d.bc) & ~(compact_even(cL | (cL >> 1)) << 16);
+                    const uint32_t lfR = word_bc(rl, wi + 1, Wl, d.bc) & ~compact_even(cR | (cR >> 1));
+                    const uint32_t gw = dilate_edges(lf, lfL, lfR, 2 * g);  // reconstruction windows
+                    const uint32_t pd = dilate_edges(fold2(pc[2 * wi], pc[2 * wi + 1]),
+                                                     fold3(word_bc(pc, 2 * wi - 1, Wc, d.bc) >> 26) << 29,
+                                                     fold3(word_bc(pc, 2 * wi + 2, Wc, d.bc) & 63u), g);
+                    const uint32_t gd = dilate_edges(fold2(gc[2 * wi], gc[2 * wi + 1]),
+                                                     fold3(word_bc(gc, 2 * wi - 1, Wc, d.bc) >> 26) << 29,
+                                                     fold3(word_bc(gc, 2 * wi + 2, Wc, d.bc) & 63u), g);
+                    lfl[wi] = lf;
+                    prl[wi] = (lf | pd) & ~ro;
+                    ghl[wi] = (gw | gd) & ~r;
+                }
+            } else {
+                const int Wc = Wl << 1;
+                const uint32_t *rc = Rn + sm.woff[l + 1], *pc = PR + sm.woff[l + 1], *gc = GH + sm.woff[l + 1];
+                for (int wi = tid; wi < Wl; wi += TS) {
+                    uint32_t r = rl[wi], ro = rol[wi];
+                    uint32_t lf = r & ~fold2(rc[2 * wi], rc[2 * wi + 1]);
+                    // leaf bits of cells 30, 31 of the left word and 0, 1 of the right word
+                    uint32_t lfL = (word_bc(rl, wi - 1, Wl, d.bc) >> 30) & ~fold_low2(word_bc(rc, 2 * wi - 1, Wc, d.bc) >> 28);
+                    uint32_t lfR = (word_bc(rl, wi + 1, Wl, d.bc) & 3u) & ~fold_low2(word_bc(rc, 2 * wi + 2, Wc, d.bc) & 15u);
+                    uint32_t gw = lf | (lf << 1) | (lf << 2) | (lf >> 1) | (lf >> 2);
+                    gw |= (lfL ? 1u : 0u) | ((lfL & 2u) ? 2u : 0u);                    // from cells 30, 31 on the left
+                    gw |= (lfR ? 0x80000000u : 0u) | ((lfR & 1u) ? 0x40000000u : 0u);  // from cells 0, 1 on the right
+                    uint32_t p = fold2(pc[2 * wi], pc[2 * wi + 1]);
+                    uint32_t pd = dilate1_edges(p, (word_bc(pc, 2 * wi - 1, Wc, d.bc) >> 30) != 0u,
+                                                (word_bc(pc, 2 * wi + 2, Wc, d.bc) & 3u) != 0u);
+                    uint32_t g = fold2(gc[2 * wi], gc[2 * wi + 1]);
+                    uint32_t gd = dilate1_edges(g, (word_bc(gc, 2 * wi - 1, Wc, d.bc) >> 30) != 0u,
+                                                (word_bc(gc, 2 * wi + 2, Wc, d.bc) & 3u) != 0u);
+                    lfl[wi] = lf;
+                    prl[wi] = (lf | pd) & ~ro;
+                    ghl[wi] = (gw | gd) & ~r;
+                }
+            }
+            sync();
+        }
+        tick(T_GRADE);
+        if (tid == 0) small_levels(Rn, Ro, grade);
+        sync();
+    }
+
+    __device__ void build_lists_dense(const uint32_t *Rn) {
+        constexpr int NW = TS / 32;
+        const int lane = tid & 31, warp = tid >> 5;
+        const int Wtot = d.Wtot;
+        int run[NLIST] = {0, 0, 0, 0};
+        if (tid == 0) sm.deplev[0] = sm.deplev[1] = 0u;  // new lists: gathered again by predict_fill
+        for (int r = 0, base = 0; base < Wtot; ++r, base += TS) {
+            const int g = base + tid;
+            const bool valid = g < Wtot;
+            int l = 0, wi = 0;
+            uint32_t m[NLIST] = {0u, 0u, 0u, 0u};
+            if (valid) {
+                level_of_word(sm, g, l, wi);
+                word_lists(Rn, g, l, m);
+            }
+            int inc[NLIST];
+#pragma unroll
+            for (int L = 0; L < NLIST; ++L) {
+                int x = __popc(m[L]);
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const int y = __shfl_up_sync(FULL, x, o);
+                    if (lane >= o) x += y;
+                }
+                inc[L] = x;
+            }
+            int(*sw)[32] = bx.scan_w[r & 1];  // alternate buffers: one barrier per round
+            if (lane == 31)
+#pragma unroll
+                for (int L = 0; L < NLIST; ++L) sw[L][warp] = inc[L];
+            sync();
+            const uint32_t pk = pack(l, 32LL * wi);
+#pragma unroll
+            for (int L = 0; L < NLIST; ++L) {
+                const int v = lane < NW ? sw[L][lane] : 0;
+                const int before = __reduce_add_sync(FULL, lane < warp ? v : 0);
+                const int tot = __reduce_add_sync(FULL, v);
+                uint32_t x = m[L];
+                int off = run[L] + before + inc[L] - __popc(x);
+                if (valid && wi == 0) sm.seg[L][l] = off;
+                uint32_t *dst = list(L);
+                while (x) {
+                    const int bit = __ffs(x) - 1;
+                    x &= x - 1u;
+                    dst[off++] = pk + (uint32_t)bit;
+                }
+                run[L] += tot;
+            }
+        }
+        if (tid == 0) {
+#pragma unroll
+            for (int L = 0; L < NLIST; ++L) sm.seg[L][d.Jmax + 1] = run[L];
             sm.nleaf = run[L_LEAF];
         }
         sync();
@@ -1485,7 +1649,7 @@ struct Worker {
     // coarse to fine, on the levels that have any.  The marks of both lists stay
     // in their masks until the next step's A2 clears them.
     __device__ void predict_fill(int L) {
-        const ListView lst = list(L);
+        const uint32_t *lst = list(L);
         const uint32_t *P = mask(L == L_GH ? M_GH : M_PRED);
         const int slot = L == L_GH ? 1 : 0;
         const int b = sm.seg[L][d.Jmin + 1], e = sm.seg[L][d.Jmax + 1];
@@ -1532,21 +1696,19 @@ struct Worker {
             }
         }
         tick(T_CANDIDATES);
-        if (!DQ && (sm.status & ST_FLUXED))
-            project_by_flux();
-        else
-            upsweep();
+        // internal cells: already projected by the last stream (D1Q2^n), else level by level
+        if (DQ || !(sm.status & ST_FLUXED)) upsweep();
         sync();
         tick(T_UPSWEEP_A);
         details();
         sync();
         tick(T_DETAILS);
-        enlarge(Rn);
+        if (sparse_on()) enlarge(Rn); else enlarge_dense(Rn);
         sync();
         tick(T_ENLARGE);
-        grade_and_mark(Rn, Ro, true);
+        if (sparse_on()) grade_and_mark(Rn, Ro, true); else grade_and_mark_dense(Rn, Ro, true);
         tick(T_GRADE_SMALL);
-        build_lists(Rn, occ(sm.cur ^ 1));
+        if (sparse_on()) build_lists(Rn, occ(sm.cur ^ 1)); else build_lists_dense(Rn);
         tick(T_LISTS);
         predict_fill(L_PRED);
         if (sparse_on()) {
@@ -1603,7 +1765,7 @@ struct Worker {
             }
         }
         const uint32_t *R = mask(sm.cur);
-        const ListView leaves = list(L_LEAF);
+        const uint32_t *leaves = list(L_LEAF);
         for (int i = tid; i < sm.nleaf; i += TS) {
             uint32_t ent = leaves[i];
             int l = ent >> KBITS;
@@ -1627,7 +1789,7 @@ struct Worker {
 #pragma unroll
             for (int h = 0; h < QMAX; ++h) {
                 if (h >= q) break;
-                const T *r = row(h, l);
+                const auto r = row(h, l);
                 const bool plus = (h & 1) == 0;  // velocity +lambda
                 bool need_first = !plus || at_left, need_last = plus || at_right;
                 T rfirst = T(0), rlast = T(0);
@@ -1635,7 +1797,7 @@ struct Worker {
                     rfirst = rlast = r[k];
                 } else {
                     T vm1 = r[wrapc(k - 1, l, d.bc)], v0 = r[k], vp1 = r[wrapc(k + 1, l, d.bc)];
-                    const T *rf = row(h, l + 1);
+                    const auto rf = row(h, l + 1);
                     if (need_first) {
                         if (at_left) {
                             rfirst = bf[0] * v0 + bf[1] * vp1;
@@ -1660,7 +1822,7 @@ struct Worker {
                         }
                     }
                 }
-                T *ph = Phi + (long long)h * (d.N + 1);
+                const auto ph = phi(h);
                 if (plus) {
                     long long ix = (k + 1) << dj;
                     if (d.bc == 0) ix &= d.N - 1;
@@ -1678,7 +1840,7 @@ struct Worker {
     // values by the level-by-level reconstruction (edge_walk) instead of tables
     __device__ __noinline__ void reconstruct_wide() {
         const uint32_t *R = mask(sm.cur);
-        const ListView leaves = list(L_LEAF);
+        const uint32_t *leaves = list(L_LEAF);
         const int g = d.gamma;
         const T *c = tab.pc[g];
         for (int i = tid; i < sm.nleaf; i += TS) {
@@ -1688,7 +1850,7 @@ struct Worker {
             const int dj = d.Jmax - l;
             const bool at_left = d.bc == 1 && k == 0, at_right = d.bc == 1 && k == (1LL << l) - 1;
             for (int h = 0; h < q; ++h) {
-                const T *rb = V + (long long)h * d.S;
+                const T *rb = V + h;
                 const bool plus = (h & 1) == 0;  // velocity +lambda
                 const bool need_first = !plus || at_left, need_last = plus || at_right;
                 T rfirst = T(0), rlast = T(0);
@@ -1696,13 +1858,13 @@ struct Worker {
                     rfirst = rlast = row(h, l)[k];
                 } else {
                     if (need_first)
-                        rfirst = g == 2 ? edge_walk<T, 2, false>(rb, d.Jmin, d.Jmax, d.bc, R, sm.woff, c, l, k)
-                                        : edge_walk<T, 3, false>(rb, d.Jmin, d.Jmax, d.bc, R, sm.woff, c, l, k);
+                        rfirst = g == 2 ? edge_walk<T, 2, false>(rb, q, d.Jmin, d.Jmax, d.bc, R, sm.woff, c, l, k)
+                                        : edge_walk<T, 3, false>(rb, q, d.Jmin, d.Jmax, d.bc, R, sm.woff, c, l, k);
                     if (need_last)
-                        rlast = g == 2 ? edge_walk<T, 2, true>(rb, d.Jmin, d.Jmax, d.bc, R, sm.woff, c, l, k)
-                                       : edge_walk<T, 3, true>(rb, d.Jmin, d.Jmax, d.bc, R, sm.woff, c, l, k);
+                        rlast = g == 2 ? edge_walk<T, 2, true>(rb, q, d.Jmin, d.Jmax, d.bc, R, sm.woff, c, l, k)
+                                       : edge_walk<T, 3, true>(rb, q, d.Jmin, d.Jmax, d.bc, R, sm.woff, c, l, k);
                 }
-                T *ph = Phi + (long long)h * (d.N + 1);
+                const auto ph = phi(h);
                 if (plus) {
                     long long ix = (k + 1) << dj;
                     if (d.bc == 0) ix &= d.N - 1;
@@ -1725,7 +1887,7 @@ struct Worker {
     // second-cell tables.
     __device__ __noinline__ void reconstruct_dq() {
         const uint32_t *R = mask(sm.cur);
-        const ListView leaves = list(L_LEAF);
+        const uint32_t *leaves = list(L_LEAF);
         for (int i = tid; i < sm.nleaf; i += TS) {
             const uint32_t ent = leaves[i];
             const int l = ent >> KBITS;
@@ -1744,14 +1906,14 @@ struct Worker {
             }
             for (int h = 1; h < q; ++h) {
                 const int w = dq_w(h), a = w < 0 ? -w : w;
-                const T *r = row(h, l);
-                T *ph = Phi + (long long)h * (d.N + 1);
+                const auto r = row(h, l);
+                const auto ph = phi(h);
                 if (dj == 0) {
                     ph[first] = r[k];
                     continue;
                 }
                 const T vm1 = r[wrapc(k - 1, l, d.bc)], v0 = r[k], vp1 = r[wrapc(k + 1, l, d.bc)];
-                const T *rf = row(h, l + 1);
+                const auto rf = row(h, l + 1);
                 // the leaf's own children (predicted), used next to a finer neighbour
                 auto children = [&](T &pe, T &po) {
                     const T tt = T(C1) * (vp1 - vm1);
@@ -1799,7 +1961,7 @@ struct Worker {
     // eta = -delta (sigma > 0) or delta - 1 (sigma < 0), V the finest values of
     // reconstruct_dq (wrapped, or clamped at a copy boundary); audit of (h, hu)
     __device__ __noinline__ void stream_dq() {
-        const ListView leaves = list(L_LEAF);
+        const uint32_t *leaves = list(L_LEAF);
         const long long N = d.N;
         auto at = [&](long long i) -> long long { return d.bc == 0 ? (i & (N - 1)) : (i < 0 ? 0 : (i >= N ? N - 1 : i)); };
         double macc[3] = {0.0, 0.0, 0.0};
@@ -1817,10 +1979,10 @@ struct Worker {
             for (int h = 0; h < QMAX; ++h)
                 if (h < q) {
                     const int w = dq_w(h);
-                    T *r = row(h, l);
+                    const auto r = row(h, l);
                     T v = r[k];
                     if (w != 0) {
-                        const T *ph = Phi + (long long)h * (N + 1);
+                        const auto ph = phi(h);
                         const int a = w < 0 ? -w : w;
                         T acc = T(0);
                         for (int dl = 1; dl <= a; ++dl) {
@@ -1875,7 +2037,7 @@ struct Worker {
                 const double dxJ = sm.dx_l[d.Jmax];
                 for (int h = 1; h < q; ++h) {
                     const int w = dq_w(h), a = w < 0 ? -w : w;
-                    const T *ph = Phi + (long long)h * (N + 1);
+                    const auto ph = phi(h);
                     double t = 0.0;
                     for (int dl = 1; dl <= a; ++dl) {
                         const long long eta = w > 0 ? -dl : dl - 1;
@@ -1923,7 +2085,7 @@ struct Worker {
             stream_dq();
             return;
         }
-        const ListView leaves = list(L_LEAF);
+        const uint32_t *leaves = list(L_LEAF);
         double macc[3] = {0.0, 0.0, 0.0};
         float fhi[3] = {0.0f, 0.0f, 0.0f}, flo[3] = {0.0f, 0.0f, 0.0f};
         bool bad = false;
@@ -1939,9 +2101,9 @@ struct Worker {
 #pragma unroll
             for (int h = 0; h < QMAX; ++h)
                 if (h < q) {
-                    const T *ph = Phi + (long long)h * (d.N + 1);
+                    const auto ph = phi(h);
                     T coef = (h & 1) ? -w : w;
-                    T *r = row(h, l);
+                    const auto r = row(h, l);
                     T v = r[k] + coef * (ph[first] - ph[next]);
                     bad |= nonfinite(v);
                     r[k] = v;
@@ -1964,6 +2126,7 @@ struct Worker {
             }
         }
         if (bad) atomicOr(&sm.status, (int)ST_NONFINITE);
+        project_by_flux_pass();  // A1 of the next adaptation, same pass
         if constexpr (sizeof(T) == 8) {
             team_sum(macc);
         } else {
@@ -1976,7 +2139,7 @@ struct Worker {
             for (int j = 0; j < nf; ++j) {
                 double flux = 0.0;
                 if (d.bc == 1) {
-                    const T *pp = Phi + (long long)(2 * j) * (d.N + 1), *pm = Phi + (long long)(2 * j + 1) * (d.N + 1);
+                    const auto pp = phi(2 * j), pm = phi(2 * j + 1);
                     flux = dxJ * (((double)pp[0] - (double)pp[d.N]) - ((double)pm[0] - (double)pm[d.N]));
                 }
                 double res = fabs(macc[j] - sm.mass[j] - flux);
@@ -1984,7 +2147,7 @@ struct Worker {
                 sm.mass[j] = macc[j];
             }
             sm.steps += 1ULL;
-            sm.status |= ST_FLUXED;  // before the barrier: every thread of the next A1 sees it
+            sm.status |= ST_FLUXED;  // before the barrier: every thread of the next adaptation sees it
         }
         sync();
     }
@@ -2030,7 +2193,11 @@ struct Worker {
             mask(M_KEEP)[g] = 0u;
             mask(M_REF)[g] = 0u;
         }
-        for (long long c = tid; c < (long long)q * d.S; c += TS) V[c] = (T)vals[c];
+        // population-major input to the cell-major layout
+        for (long long c = tid; c < (long long)q * d.S; c += TS) {
+            const long long hh = c / d.S, cell = c - hh * d.S;
+            V[cell * q + hh] = (T)vals[c];
+        }
         if (tid == 0) sm.cur = M_R0;
         sync();
         finish_init();
@@ -2054,7 +2221,7 @@ struct Worker {
         grade_and_mark(R, R, false);  // PRED empty: the tree is its own old tree
         build_lists(R, occ(sm.cur));
         // FP64 totals of the initial leaves
-        const ListView leaves = list(L_LEAF);
+        const uint32_t *leaves = list(L_LEAF);
         double macc[3] = {0.0, 0.0, 0.0};
         for (int i = tid; i < sm.nleaf; i += TS) {
             uint32_t ent = leaves[i];
@@ -2082,10 +2249,9 @@ struct Worker {
             sm.near_ties = 0;
             sm.updates = 0ULL;
             sm.steps = 0ULL;
-            sm.passes = 0ULL;
         }
+        if (tid == TS - 1) sm.passes = 0ULL;  // the thread that counts the barriers
         sync();
-        npass = 0;
     }
 
     // ---- multiresolution reconstruction on the finest level (measurement) ----
@@ -2181,6 +2347,11 @@ __device__ void load_instance(TeamSmem<T> &sm, const InstDesc &dg, int tid) {
 
 template <typename T, int TS>
 __device__ void store_instance(TeamSmem<T> &sm, int tid) {
+    // the barrier count of the last pass is written after that pass's barrier
+    if constexpr (TS == 32)
+        __syncwarp();
+    else
+        __syncthreads();
     InstState &st = *sm.d.st;
     if (tid == 0) {
         st.cur = sm.cur;
@@ -2208,8 +2379,8 @@ __device__ void store_instance(TeamSmem<T> &sm, int tid) {
 // one instance for the launch's steps
 template <typename T, int NF, int TS, bool WIDE, int SPM>
 __device__ __forceinline__ void run_instance(TeamSmem<T> &sm, const Tables<T> &tab, BlockScratch &bx, const LaunchArgs &a, int tid,
-                             uint32_t *masks, uint32_t *slist, int lcap) {
-    Worker<T, NF, TS, WIDE, SPM> w(sm, tab, bx, tid, masks, slist, lcap);
+                             uint32_t *masks) {
+    Worker<T, NF, TS, WIDE, SPM> w(sm, tab, bx, tid, masks);
     if (a.phases & PH_INIT_FULL) w.init_full((const double *)a.aux0 + sm.d.m_off);
     if (a.phases & PH_INIT_STATE) w.init_state((const unsigned char *)a.aux0, (const double *)a.aux1);
     for (int n = 0; n < a.nsteps; ++n) {
@@ -2217,7 +2388,6 @@ __device__ __forceinline__ void run_instance(TeamSmem<T> &sm, const Tables<T> &t
         if (a.phases & PH_STEP) w.lbm_step();
     }
     if (a.phases & PH_FINEST) w.finest((double *)a.aux0);
-    if (tid == 0) sm.passes += w.npass;
 }
 
 // Bitmasks live in shared memory (smask, room for `cap` words per mask) when the
@@ -2227,15 +2397,8 @@ __device__ __forceinline__ void run_instance(TeamSmem<T> &sm, const Tables<T> &t
 // every step.
 template <typename T, int TS, bool WIDE, bool SCALAR, int SPM>
 __device__ void run_team(TeamSmem<T> &sm, const Tables<T> &tab, BlockScratch &bx, const LaunchArgs &a,
-                         const InstDesc &dg, int tid, uint32_t *smask, int cap, uint32_t *slist, int lcap) {
+                         const InstDesc &dg, int tid, uint32_t *smask, int cap) {
     load_instance<T, TS, SPM>(sm, dg, tid);
-    // the first lcap entries of every cell list live in shared memory for the launch
-    if (slist)
-        for (int L = 0; L < NLIST; ++L) {
-            const int n = min(lcap, sm.seg[L][sm.d.Jmax + 1]);
-            const uint32_t *gl = sm.d.lists + sm.d.list_off[L];
-            for (int i = tid; i < n; i += TS) slist[L * lcap + i] = gl[i];
-        }
     const int W = sm.d.Wtot, OW = sm.d.OW;
     const long long region = smem_region_words(W, OW);
     const bool local = smask != nullptr && region <= cap;
@@ -2260,24 +2423,18 @@ __device__ void run_team(TeamSmem<T> &sm, const Tables<T> &tab, BlockScratch &bx
     }
     __syncthreads();
     if constexpr (SCALAR) {
-        run_instance<T, 1, TS, WIDE, SPM>(sm, tab, bx, a, tid, masks, slist, lcap);
+        run_instance<T, 1, TS, WIDE, SPM>(sm, tab, bx, a, tid, masks);
     } else {
         // scheme variant: D1Q2^nf, or D1Q3 / D1Q5 shallow water (equilibria 4, 5)
         const int var = sm.d.eq == 4 ? 4 : sm.d.eq == 5 ? 5 : sm.d.nf;
         switch (var) {
-        case 1: run_instance<T, 1, TS, WIDE, SPM>(sm, tab, bx, a, tid, masks, slist, lcap); break;
-        case 2: run_instance<T, 2, TS, WIDE, SPM>(sm, tab, bx, a, tid, masks, slist, lcap); break;
-        case 4: run_instance<T, 4, TS, WIDE, SPM>(sm, tab, bx, a, tid, masks, slist, lcap); break;
-        case 5: run_instance<T, 5, TS, WIDE, SPM>(sm, tab, bx, a, tid, masks, slist, lcap); break;
-        default: run_instance<T, 3, TS, WIDE, SPM>(sm, tab, bx, a, tid, masks, slist, lcap); break;
+        case 1: run_instance<T, 1, TS, WIDE, SPM>(sm, tab, bx, a, tid, masks); break;
+        case 2: run_instance<T, 2, TS, WIDE, SPM>(sm, tab, bx, a, tid, masks); break;
+        case 4: run_instance<T, 4, TS, WIDE, SPM>(sm, tab, bx, a, tid, masks); break;
+        case 5: run_instance<T, 5, TS, WIDE, SPM>(sm, tab, bx, a, tid, masks); break;
+        default: run_instance<T, 3, TS, WIDE, SPM>(sm, tab, bx, a, tid, masks); break;
         }
     }
-    if (slist)
-        for (int L = 0; L < NLIST; ++L) {
-            const int n = min(lcap, sm.seg[L][sm.d.Jmax + 1]);
-            uint32_t *gl = sm.d.lists + sm.d.list_off[L];
-            for (int i = tid; i < n; i += TS) gl[i] = slist[L * lcap + i];
-        }
     if (local) {
         uint32_t *gr = sm.d.masks + (long long)sm.cur * W;
         uint32_t *gp = sm.d.masks + (long long)M_PRED * W, *gg = sm.d.masks + (long long)M_GH * W;
@@ -2307,10 +2464,9 @@ __global__ void __launch_bounds__(NT, MINB) mr_persistent(LaunchArgs a) {
     constexpr int SPM = KIND == K_LARGE ? 2 : WIDE ? 1 : 0;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     BlockSmem<T, NT> &bs = *reinterpret_cast<BlockSmem<T, NT> *>(smem_raw);
-    uint32_t *sdyn = reinterpret_cast<uint32_t *>(smem_raw + ((sizeof(BlockSmem<T, NT>) + 15) / 16) * 16);
-    uint32_t *smask = a.smem_mask_words > 0 ? sdyn : nullptr;
-    const int lcap = a.smem_list_words / NLIST;
-    uint32_t *slist = lcap > 0 ? sdyn + a.smem_mask_words : nullptr;
+    uint32_t *smask = a.smem_mask_words > 0
+                          ? reinterpret_cast<uint32_t *>(smem_raw + ((sizeof(BlockSmem<T, NT>) + 15) / 16) * 16)
+                          : nullptr;
     {
         const uint32_t *src = (const uint32_t *)a.tables;
         uint32_t *dst = (uint32_t *)&bs.tab;
@@ -2323,7 +2479,7 @@ __global__ void __launch_bounds__(NT, MINB) mr_persistent(LaunchArgs a) {
         __syncthreads();
         if (idx >= a.n) return;
         run_team<T, NT, WIDE, KIND == K_SCALAR, SPM>(bs.team, bs.tab, bs.scratch, a, a.descs[a.order[idx]], threadIdx.x, smask,
-                                                a.smem_mask_words, slist, lcap);
+                                                a.smem_mask_words);
     }
 }
 
@@ -2378,7 +2534,7 @@ __global__ void __launch_bounds__(NT, MINB) mr_persistent(LaunchArgs a) {
     int mrg_launch_##TAG(int grid, const mrg::LaunchArgs &a, cudaStream_t s, int prio) {           \
         int rc = mrg_attr_##TAG();                                                                \
         if (rc) return rc;                                                                        \
-        const size_t dyn = mrg_dyn_##TAG(a.smem_mask_words + a.smem_list_words);                   \
+        const size_t dyn = mrg_dyn_##TAG(a.smem_mask_words);                                       \
         switch (a.kind) {                                                                         \
         case mrg::K_FAST: return mrg_go_##TAG<MINB, mrg::K_FAST>(grid, a, dyn, s, prio);           \
         case mrg::K_GENERAL: return mrg_go_##TAG<MINB_G, mrg::K_GENERAL>(grid, a, dyn, s, prio);   \

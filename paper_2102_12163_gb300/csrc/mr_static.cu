@@ -211,10 +211,6 @@ extern "C" mr_status mr_run_static(const mr_instance_desc *desc, int precision, 
     a.tables = base + oTab + (fp32 ? sizeof(Tables<double>) : 0);
     const long long sregion = smem_region_words(W, OW);
     a.smem_mask_words = sregion <= fit ? (int)sregion : 0;
-    // the rest of the shared memory holds the first entries of the cell lists
-    long long lw = fit - a.smem_mask_words;
-    lw = lw < NLIST * 256LL ? lw : NLIST * 256LL;
-    a.smem_list_words = lw > 0 ? (int)(lw / NLIST * NLIST) : 0;
     a.kind = d.gamma > 1 ? K_GENERAL : d.collision != 0 ? K_RECOLL : W >= CW_MIN_WORDS ? K_LARGE : K_FAST;
     const int phases[3] = {PH_INIT_FULL, PH_ADAPT | PH_STEP, PH_FINEST};
     const int steps[3] = {0, nsteps, 0};
