@@ -1279,7 +1279,7 @@ struct Worker {
             sync();
         }
         tick(T_GRADE);
-        if (tid == 0) small_levels(Rn, Ro, grade);
+        if (tid == 0 && d.Jmin <= 5) small_levels(Rn, Ro, grade);
         sync();
     }
 
@@ -1467,7 +1467,9 @@ struct Worker {
         uint32_t *LF = mask(M_LEAF), *PR = mask(M_PRED), *GH = mask(M_GH);
         const int g = d.gamma;
         const int lbig = d.Jmin > 6 ? d.Jmin : 6;
-        for (int l = d.Jmax; l >= lbig; --l) {
+        // gamma = 1: the levels of at most 32 words go to one warp (grade_warp)
+        const int lwarp = WIDE ? lbig - 1 : (d.Jmax < 10 ? d.Jmax : 10);
+        for (int l = d.Jmax; l >= lbig && l > lwarp; --l) {
             const int Wl = 1 << (l - 5);
             const uint32_t *rl = Rn + sm.woff[l];
             if (grade && l > d.Jmin + 1) {
@@ -1544,9 +1546,97 @@ struct Worker {
             }
             sync();
         }
+        if constexpr (!WIDE)
+            if (tid < 32 && lwarp >= lbig) grade_warp(Rn, Ro, grade, lwarp, lbig);
         tick(T_GRADE);
-        if (tid == 0) small_levels(Rn, Ro, grade);
+        if (tid == 0 && d.Jmin <= 5) small_levels(Rn, Ro, grade);
         sync();
+    }
+
+    // Grading and marking of the levels ltop .. lbot of at most 32 words each
+    // (gamma = 1) by one warp, without block barriers: lane i holds word i of
+    // the current level and words 2i, 2i + 1 of the level below it (R, PR, GH)
+    // in registers, neighbouring and child words arrive by shuffles (wrapped
+    // or empty beyond the domain, as word_bc), and the results are stored for
+    // the list compaction and the small levels.  The same operations as the
+    // block-wide sweep, level for level.
+    __device__ __noinline__ void grade_warp(uint32_t *Rn, const uint32_t *Ro, bool grade, int ltop, int lbot) {
+        uint32_t *LF = mask(M_LEAF), *PR = mask(M_PRED), *GH = mask(M_GH);
+        const int lane = tid;  // tid < 32
+        const int bc = d.bc;
+        const int Wt = 1 << (ltop - 5);
+        // words 2 lane, 2 lane + 1 of level ltop + 1 (final: graded and marked by the block)
+        uint32_t rc0 = 0u, rc1 = 0u, pc0 = 0u, pc1 = 0u, gc0 = 0u, gc1 = 0u;
+        if (ltop < d.Jmax && lane < Wt) {
+            const int o = sm.woff[ltop + 1] + 2 * lane;
+            rc0 = Rn[o];
+            rc1 = Rn[o + 1];
+            pc0 = PR[o];
+            pc1 = PR[o + 1];
+            gc0 = GH[o];
+            gc1 = GH[o + 1];
+        }
+        uint32_t r = lane < Wt ? Rn[sm.woff[ltop] + lane] : 0u;  // level ltop, graded from ltop + 1
+        for (int l = ltop; l >= lbot; --l) {
+            const int Wl = 1 << (l - 5);  // 2 .. 32 words
+            const bool act = lane < Wl;
+            const uint32_t ro = act ? Ro[sm.woff[l] + lane] : 0u;
+            // word j of a level of Wl words whose word q lane q holds in v
+            auto word = [&](uint32_t v, int j) -> uint32_t {
+                const bool out = j < 0 || j >= Wl;
+                const int src = bc == 0 ? ((j + Wl) & (Wl - 1)) : (out ? 0 : j);
+                const uint32_t x = __shfl_sync(FULL, v, src);
+                return (bc != 0 && out) ? 0u : x;
+            };
+            // grading of level l - 1: parent word wp = lane from words 2wp - 1 .. 2wp + 2 of level l
+            const uint32_t c0 = word(r, 2 * lane), c1 = word(r, 2 * lane + 1);
+            const uint32_t cL = word(r, 2 * lane - 1), cR = word(r, 2 * lane + 2);
+            uint32_t rpn = 0u;
+            if (l > d.Jmin) {
+                const int Wp = Wl >> 1;
+                uint32_t hp = lane < Wp ? Rn[sm.woff[l - 1] + lane] : 0u;  // enlarged set of level l - 1
+                if (grade && l > d.Jmin + 1 && lane < Wp)
+                    hp |= pairexpand(dilate1_edges(fold2(c0, c1), (cL >> 30) != 0u, (cR & 3u) != 0u));
+                if (lane < Wp) Rn[sm.woff[l - 1] + lane] = hp;
+                rpn = lane < Wp ? hp : 0u;
+            }
+            // leaf, transfer and ghost marks of level l
+            uint32_t lf, pr, gh = 0u;
+            if (l == d.Jmax) {
+                lf = r;
+                pr = r & ~ro;
+            } else {
+                const uint32_t rl0 = word(r, lane - 1), rl1 = word(r, lane + 1);
+                const uint32_t rcL = word(rc1, lane - 1), rcR = word(rc0, lane + 1);  // words 2 lane - 1, 2 lane + 2 below
+                const uint32_t pcL = word(pc1, lane - 1), pcR = word(pc0, lane + 1);
+                const uint32_t gcL = word(gc1, lane - 1), gcR = word(gc0, lane + 1);
+                lf = r & ~fold2(rc0, rc1);
+                const uint32_t lfL = (rl0 >> 30) & ~fold_low2(rcL >> 28);
+                const uint32_t lfR = (rl1 & 3u) & ~fold_low2(rcR & 15u);
+                uint32_t gw = lf | (lf << 1) | (lf << 2) | (lf >> 1) | (lf >> 2);
+                gw |= (lfL ? 1u : 0u) | ((lfL & 2u) ? 2u : 0u);
+                gw |= (lfR ? 0x80000000u : 0u) | ((lfR & 1u) ? 0x40000000u : 0u);
+                const uint32_t pd = dilate1_edges(fold2(pc0, pc1), (pcL >> 30) != 0u, (pcR & 3u) != 0u);
+                const uint32_t gd = dilate1_edges(fold2(gc0, gc1), (gcL >> 30) != 0u, (gcR & 3u) != 0u);
+                pr = (lf | pd) & ~ro;
+                gh = (gw | gd) & ~r;
+            }
+            if (act) {
+                const int o = sm.woff[l] + lane;
+                LF[o] = lf;
+                PR[o] = pr;
+                GH[o] = gh;
+            }
+            // the next level (l - 1): its lane i holds words 2i, 2i + 1 of level l
+            rc0 = c0;
+            rc1 = c1;
+            pc0 = __shfl_sync(FULL, pr, (2 * lane) & 31);
+            pc1 = __shfl_sync(FULL, pr, (2 * lane + 1) & 31);
+            gc0 = __shfl_sync(FULL, gh, (2 * lane) & 31);
+            gc1 = __shfl_sync(FULL, gh, (2 * lane + 1) & 31);
+            r = rpn;
+        }
+        __syncwarp();
     }
 
     __device__ void build_lists_dense(const uint32_t *Rn) {
