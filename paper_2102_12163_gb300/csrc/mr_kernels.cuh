@@ -1654,30 +1654,36 @@ struct Worker {
                 level_of_word(sm, g, l, wi);
                 word_lists(Rn, g, l, m);
             }
-            int inc[NLIST];
+            // the four lists' counts two per value, in 16-bit fields (a round's
+            // totals are at most 1024 x 32 < 2^16): half the scan steps and reductions
+            uint32_t x01 = (uint32_t)__popc(m[0]) | ((uint32_t)__popc(m[1]) << 16);
+            uint32_t x23 = (uint32_t)__popc(m[2]) | ((uint32_t)__popc(m[3]) << 16);
 #pragma unroll
-            for (int L = 0; L < NLIST; ++L) {
-                int x = __popc(m[L]);
-#pragma unroll
-                for (int o = 1; o < 32; o <<= 1) {
-                    const int y = __shfl_up_sync(FULL, x, o);
-                    if (lane >= o) x += y;
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t y01 = __shfl_up_sync(FULL, x01, o), y23 = __shfl_up_sync(FULL, x23, o);
+                if (lane >= o) {
+                    x01 += y01;
+                    x23 += y23;
                 }
-                inc[L] = x;
             }
             int(*sw)[32] = bx.scan_w[r & 1];  // alternate buffers: one barrier per round
-            if (lane == 31)
-#pragma unroll
-                for (int L = 0; L < NLIST; ++L) sw[L][warp] = inc[L];
+            if (lane == 31) {
+                sw[0][warp] = (int)x01;
+                sw[1][warp] = (int)x23;
+            }
             sync();
+            const uint32_t v01 = lane < NW ? (uint32_t)sw[0][lane] : 0u, v23 = lane < NW ? (uint32_t)sw[1][lane] : 0u;
+            const uint32_t b01 = __reduce_add_sync(FULL, lane < warp ? v01 : 0u);
+            const uint32_t b23 = __reduce_add_sync(FULL, lane < warp ? v23 : 0u);
+            const uint32_t t01 = __reduce_add_sync(FULL, v01), t23 = __reduce_add_sync(FULL, v23);
+            const int inc[NLIST] = {(int)(x01 & 0xFFFFu), (int)(x01 >> 16), (int)(x23 & 0xFFFFu), (int)(x23 >> 16)};
+            const int before[NLIST] = {(int)(b01 & 0xFFFFu), (int)(b01 >> 16), (int)(b23 & 0xFFFFu), (int)(b23 >> 16)};
+            const int tot[NLIST] = {(int)(t01 & 0xFFFFu), (int)(t01 >> 16), (int)(t23 & 0xFFFFu), (int)(t23 >> 16)};
             const uint32_t pk = pack(l, 32LL * wi);
 #pragma unroll
             for (int L = 0; L < NLIST; ++L) {
-                const int v = lane < NW ? sw[L][lane] : 0;
-                const int before = __reduce_add_sync(FULL, lane < warp ? v : 0);
-                const int tot = __reduce_add_sync(FULL, v);
                 uint32_t x = m[L];
-                int off = run[L] + before + inc[L] - __popc(x);
+                int off = run[L] + before[L] + inc[L] - __popc(x);
                 if (valid && wi == 0) sm.seg[L][l] = off;
                 uint32_t *dst = list(L);
                 while (x) {
@@ -1685,7 +1691,7 @@ struct Worker {
                     x &= x - 1u;
                     dst[off++] = pk + (uint32_t)bit;
                 }
-                run[L] += tot;
+                run[L] += tot[L];
             }
         }
         if (tid == 0) {
