@@ -85,14 +85,17 @@ def host_cores():
     return usable, os.cpu_count() or usable
 
 
-def profiled_traffic(workload: str, precision: str):
+def profiled_traffic(workload: str, precision: str, graph_steps: int):
     """DRAM bytes per leaf update from the committed ncu record
-    (profiles/traffic.json), if it was taken on the current kernel source."""
+    (profiles/traffic.json) of a launch of the same number of steps, if it was
+    taken on the current kernel source.  The steps per launch are part of the
+    key because an instance's values stay in L2 between the steps of one launch:
+    the DRAM bytes per update fall as the launch grows."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         with open(path) as fh:
             j = json.load(fh)
-        e = j[f"{workload}:{precision}"]
+        e = j[f"{workload}:{precision}:g{graph_steps}"]
         if e.get("source_hash") != source_hash():
             return None
         return e
@@ -650,7 +653,8 @@ def main():
 
     def roof(r, prec):
         achieved = r["bytes_alg"] / r["dt"] / 1e9
-        tr = profiled_traffic(args.workload, prec) if len(insts) == 4096 or args.workload != "batch" else None
+        tr = (profiled_traffic(args.workload, prec, r["graph_steps"])
+              if len(insts) == 4096 or args.workload != "batch" else None)
         launches = max(1, r["launches"])
         per_launch_updates = r["updates"] / launches
         out = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,

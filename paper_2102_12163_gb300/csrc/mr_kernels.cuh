@@ -219,21 +219,49 @@ __device__ __forceinline__ void level_of_word(const TeamSmem<T> &sm, int g, int 
 // ---------------------------------------------------------------------------
 // scheme: vectorial D1Q2^n (Section 2.1, equilibria of Sections 5.1 and 5.3)
 
-// x * 2^k, bit for bit the correctly rounded product, in integer arithmetic
-// where the exponent field allows (normal operand and result) and with the
-// multiply otherwise: GB300's FP64 units are scarce, integer units are not.
+// 2^-n exactly, built from its exponent field (0 <= n <= 126): no conversion
+// instruction, which for a double would occupy GB300's scarce FP64 units
+template <typename T>
+__device__ __forceinline__ T pow2m(int n) {
+    if constexpr (sizeof(T) == 8)
+        return __longlong_as_double((long long)(1023 - n) << 52);
+    else
+        return __int_as_float((127 - n) << 23);
+}
+
+// x * 2^k (|k| <= 1022), bit for bit the correctly rounded product, in integer
+// arithmetic where the exponent field allows (zero, or a normal operand and
+// result) and with the multiply otherwise: GB300's FP64 units are scarce,
+// integer units are not.
 __device__ __forceinline__ double scale2(double x, int k) {
     const unsigned long long b = (unsigned long long)__double_as_longlong(x);
     const int e = (int)((b >> 52) & 0x7FFull);
+    if ((b << 1) == 0ull) return x;
     if (e > 0 && e < 0x7FF && e + k > 0 && e + k < 0x7FF)
         return __longlong_as_double((long long)(b + ((unsigned long long)(long long)k << 52)));
-    return x * ldexp(1.0, k);
+    return x * __longlong_as_double((long long)(1023 + k) << 52);
 }
 __device__ __forceinline__ float scale2(float x, int k) { return x * ldexpf(1.0f, k); }
+
+// x / 2, bit for bit the product x * 0.5, on the integer units: an exponent
+// field e >= 2 loses one; for e <= 1 the magnitude bits are the value in units
+// of 2^-1074 (the implicit bit included), halved with ties to even (which also
+// carries into the smallest normal number); infinities and NaNs pass unchanged
+__device__ __forceinline__ double half_f64(double x) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    const unsigned long long sign = b & 0x8000000000000000ull, mag = b ^ sign;
+    const unsigned e = (unsigned)(mag >> 52);
+    unsigned long long r;
+    if (e >= 2u)
+        r = e == 0x7FFu ? mag : mag - (1ull << 52);
+    else
+        r = (mag >> 1) + ((mag & 1ull) & ((mag >> 1) & 1ull));
+    return __longlong_as_double((long long)(sign | r));
+}
 template <typename T>
 __device__ __forceinline__ T half_of(T x) {
     if constexpr (sizeof(T) == 8)
-        return scale2(x, -1);
+        return half_f64(x);
     else
         return T(0.5) * x;
 }
@@ -829,7 +857,7 @@ struct Worker {
                 for (int o = 16; o > 0; o >>= 1) acc[r] = acc[r] + __shfl_xor_sync(FULL, acc[r], o);
             if (lane == 0)
 #pragma unroll
-                for (int r = 0; r < NR; ++r) Phi[r * stride + i] = acc[r] * (T)ldexpf(1.0f, -dj);
+                for (int r = 0; r < NR; ++r) Phi[r * stride + i] = acc[r] * pow2m<T>(dj);
         }
         sync();
         for (int i = tid; i < sm.nleaf; i += TS) {
@@ -919,7 +947,7 @@ struct Worker {
             const int dj = d.Jmax - l;
             long long first = k << dj, next = (k + 1) << dj;
             if (d.bc == 0) next &= d.N - 1;
-            const T w = (T)ldexpf(1.0f, -dj);
+            const T w = pow2m<T>(dj);
 #pragma unroll
             for (int h = 0; h < QMAX; ++h)
                 if (h < q) {
@@ -1894,27 +1922,56 @@ struct Worker {
                 } else {
                     T vm1 = r[wrapc(k - 1, l, d.bc)], v0 = r[k], vp1 = r[wrapc(k + 1, l, d.bc)];
                     const auto rf = row(h, l + 1);
+                    // one sum of four products for both stencils, so that a warp whose
+                    // leaves mix them evaluates it once: next to a finer neighbour the
+                    // leaf's own children (predicted) enter with the weights t1, else
+                    // the cells of level l with the weights cf
                     if (need_first) {
                         if (at_left) {
                             rfirst = bf[0] * v0 + bf[1] * vp1;
-                        } else if (fin_l) {
-                            // next to a finer neighbour: the leaf's own children (predicted) enter
-                            const T tt = T(C1) * (vp1 - vm1);
-                            long long c = 2 * wrapc(k - 1, l, d.bc);
-                            rfirst = dot4(t1[0], rf[c], t1[1], rf[c + 1], t1[2], v0 + tt, t1[3], v0 - tt);
                         } else {
-                            rfirst = dot4(cf[0], r[wrapc(k - 2, l, d.bc)], cf[1], vm1, cf[2], v0, cf[3], vp1);
+                            T x0, x1, x2, x3;
+                            const T *wt;
+                            if (fin_l) {
+                                const T tt = T(C1) * (vp1 - vm1);
+                                const long long c = 2 * wrapc(k - 1, l, d.bc);
+                                x0 = rf[c];
+                                x1 = rf[c + 1];
+                                x2 = v0 + tt;
+                                x3 = v0 - tt;
+                                wt = t1;
+                            } else {
+                                x0 = r[wrapc(k - 2, l, d.bc)];
+                                x1 = vm1;
+                                x2 = v0;
+                                x3 = vp1;
+                                wt = cf;
+                            }
+                            rfirst = dot4(wt[0], x0, wt[1], x1, wt[2], x2, wt[3], x3);
                         }
                     }
                     if (need_last) {
                         if (at_right) {
                             rlast = bf[0] * v0 + bf[1] * vm1;
-                        } else if (fin_r) {
-                            const T tt = T(C1) * (vp1 - vm1);
-                            long long c = 2 * wrapc(k + 1, l, d.bc);
-                            rlast = dot4(t1[3], v0 + tt, t1[2], v0 - tt, t1[1], rf[c], t1[0], rf[c + 1]);
                         } else {
-                            rlast = dot4(cf[3], vm1, cf[2], v0, cf[1], vp1, cf[0], r[wrapc(k + 2, l, d.bc)]);
+                            T x0, x1, x2, x3;
+                            const T *wt;
+                            if (fin_r) {
+                                const T tt = T(C1) * (vp1 - vm1);
+                                const long long c = 2 * wrapc(k + 1, l, d.bc);
+                                x0 = v0 + tt;
+                                x1 = v0 - tt;
+                                x2 = rf[c];
+                                x3 = rf[c + 1];
+                                wt = t1;
+                            } else {
+                                x0 = vm1;
+                                x1 = v0;
+                                x2 = vp1;
+                                x3 = r[wrapc(k + 2, l, d.bc)];
+                                wt = cf;
+                            }
+                            rlast = dot4(wt[3], x0, wt[2], x1, wt[1], x2, wt[0], x3);
                         }
                     }
                 }
@@ -2010,34 +2067,52 @@ struct Worker {
                 }
                 const T vm1 = r[wrapc(k - 1, l, d.bc)], v0 = r[k], vp1 = r[wrapc(k + 1, l, d.bc)];
                 const auto rf = row(h, l + 1);
-                // the leaf's own children (predicted), used next to a finer neighbour
-                auto children = [&](T &pe, T &po) {
-                    const T tt = T(C1) * (vp1 - vm1);
-                    pe = v0 + tt;
-                    po = v0 - tt;
-                };
-                // cell `sec` (0: first / last, 1: second from that edge) next to the left or right edge
+                // cell `sec` (0: first / last, 1: second from that edge) next to the left or right
+                // edge: one sum of four products for both stencils (as in reconstruct_edges), next
+                // to a finer neighbour with the leaf's own (predicted) children and the weights t1
                 auto from_left = [&](int sec) -> T {
                     const T *bf = sec ? tab.bf2[dj] : tab.bf[dj], *t1 = sec ? tab.t12[dj] : tab.t1[dj],
                             *cf = sec ? tab.cf2[dj] : tab.cf[dj];
                     if (at_left) return bf[0] * v0 + bf[1] * vp1;
+                    T x0, x1, x2, x3;
+                    const T *wt;
                     if (fin_l) {
-                        T pe, po;
-                        children(pe, po);
-                        return dot4(t1[0], rf[cl], t1[1], rf[cl + 1], t1[2], pe, t1[3], po);
+                        const T tt = T(C1) * (vp1 - vm1);
+                        x0 = rf[cl];
+                        x1 = rf[cl + 1];
+                        x2 = v0 + tt;
+                        x3 = v0 - tt;
+                        wt = t1;
+                    } else {
+                        x0 = r[wrapc(k - 2, l, d.bc)];
+                        x1 = vm1;
+                        x2 = v0;
+                        x3 = vp1;
+                        wt = cf;
                     }
-                    return dot4(cf[0], r[wrapc(k - 2, l, d.bc)], cf[1], vm1, cf[2], v0, cf[3], vp1);
+                    return dot4(wt[0], x0, wt[1], x1, wt[2], x2, wt[3], x3);
                 };
                 auto from_right = [&](int sec) -> T {
                     const T *bf = sec ? tab.bf2[dj] : tab.bf[dj], *t1 = sec ? tab.t12[dj] : tab.t1[dj],
                             *cf = sec ? tab.cf2[dj] : tab.cf[dj];
                     if (at_right) return bf[0] * v0 + bf[1] * vm1;
+                    T x0, x1, x2, x3;
+                    const T *wt;
                     if (fin_r) {
-                        T pe, po;
-                        children(pe, po);
-                        return dot4(t1[3], pe, t1[2], po, t1[1], rf[cr], t1[0], rf[cr + 1]);
+                        const T tt = T(C1) * (vp1 - vm1);
+                        x0 = v0 + tt;
+                        x1 = v0 - tt;
+                        x2 = rf[cr];
+                        x3 = rf[cr + 1];
+                        wt = t1;
+                    } else {
+                        x0 = vm1;
+                        x1 = v0;
+                        x2 = vp1;
+                        x3 = r[wrapc(k + 2, l, d.bc)];
+                        wt = cf;
                     }
-                    return dot4(cf[3], vm1, cf[2], v0, cf[1], vp1, cf[0], r[wrapc(k + 2, l, d.bc)]);
+                    return dot4(wt[3], x0, wt[2], x1, wt[1], x2, wt[0], x3);
                 };
                 if (w > 0) {
                     ph[last] = from_right(0);
@@ -2069,7 +2144,7 @@ struct Worker {
             const long long k = ent & KMASK;
             const int dj = d.Jmax - l;
             const long long first = k << dj, next = (k + 1) << dj;
-            const T wgt = (T)ldexpf(1.0f, -dj);
+            const T wgt = pow2m<T>(dj);
             T fn[QMAX];
 #pragma unroll
             for (int h = 0; h < QMAX; ++h)
@@ -2103,7 +2178,7 @@ struct Worker {
                 macc[1] += sm.dx_l[l] * m1;
             } else {
                 // exact per-leaf sums of f and of w f in float-float, scaled by 2^-l
-                const float sc = ldexpf(1.0f, -l);
+                const float sc = pow2m<float>(l);
                 float a0 = 0.0f, e0 = 0.0f, a1 = 0.0f, e1 = 0.0f;
 #pragma unroll
                 for (int h = 0; h < QMAX; ++h)
@@ -2192,7 +2267,7 @@ struct Worker {
             int dj = d.Jmax - l;
             long long first = k << dj, next = (k + 1) << dj;
             if (d.bc == 0) next &= d.N - 1;
-            const T w = (T)ldexpf(1.0f, -dj);
+            const T w = pow2m<T>(dj);
             T fn[QMAX];
 #pragma unroll
             for (int h = 0; h < QMAX; ++h)
@@ -2211,7 +2286,7 @@ struct Worker {
                 for (int j = 0; j < 3; ++j)
                     if (j < nf) macc[j] += dx * ((double)fn[2 * j] + (double)fn[2 * j + 1]);
             } else {
-                const float sc = ldexpf(1.0f, -l);
+                const float sc = pow2m<float>(l);
 #pragma unroll
                 for (int j = 0; j < 3; ++j)
                     if (j < nf) {
