@@ -99,10 +99,12 @@ struct InstDesc {
 // words of the mask region of an instance: NMASK bitmasks, the candidate-word
 // list and two occupancy bitmaps
 inline long long mask_region_words(int Wtot, int OW) { return (long long)(NMASK + 1) * Wtot + 2LL * OW; }
-// Instances with at least this many mask words per bitmask run their word
-// passes over the step's candidate words; smaller ones visit every word, which
-// costs less than building the candidate list (measured on the Jmax 8..14 batch
-// and the single instances).
+// gamma = 1 instances with the leaves collision and at least this many mask
+// words per bitmask run their word passes over the step's candidate words
+// (K_LARGE); smaller ones visit every word, which costs less than building the
+// candidate list (measured on the Jmax 8..14 batch and the single instances).
+// The wide-stencil and reconstructed-collision variants visit every word at
+// any size.
 constexpr int CW_MIN_WORDS = 2048;
 // words of the mask region a block keeps in shared memory: without candidate
 // words the list and the occupancy bitmaps are not used
@@ -173,7 +175,7 @@ struct LaunchArgs {
 // from blocks in flight, the wide stencils from registers); K_LARGE: the code of
 // K_FAST for the instances with at least CW_MIN_WORDS mask words per bitmask,
 // whose word passes visit the step's candidate words (the code that builds
-// them stays out of K_FAST and K_SCALAR, which it slowed down).
+// them stays out of the other variants, which it slowed down).
 constexpr int K_FAST = 0, K_GENERAL = 1, K_SCALAR = 2, K_RECOLL = 3, K_LARGE = 4, NKIND = 5;
 
 }  // namespace mrg

@@ -592,8 +592,9 @@ struct SRow {
 };
 
 // WIDE: prediction stencils gamma = 2, 3 (the gamma = 1 code is a separate instantiation)
-// SPM: word passes over candidate words never (0), for the instances with at
-// least CW_MIN_WORDS words per bitmask (1), always (2)
+// SPM: word passes over every word (0) or over candidate words (1, the
+// large-instance variant K_LARGE alone: code that a kernel carries costs it
+// even where it does not run)
 template <typename T, int NF, int TS, bool WIDE, int SPM>
 struct Worker {
     static constexpr bool WARP = TS == 32;
@@ -659,14 +660,7 @@ struct Worker {
     __device__ __forceinline__ uint32_t *cwl() { return M + (long long)NMASK * d.Wtot; }
     // i-th word of the step's word passes: a candidate word, or word i itself
     __device__ __forceinline__ int cw_at(int i) { return sparse_on() ? (int)cwl()[i] : i; }
-    __device__ __forceinline__ bool sparse_on() const {
-        if constexpr (SPM == 0)
-            return false;
-        else if constexpr (SPM == 2)
-            return true;
-        else
-            return sm.sparse != 0;
-    }
+    __device__ __forceinline__ bool sparse_on() const { return SPM != 0; }
     // occupancy bitmap of tree buffer b (M_R0 or M_R1): bit wi & 31 of word ooff[l] + (wi >> 5) is set
     // when word wi of level l of that tree holds a cell
     __device__ __forceinline__ uint32_t *occ(int b) { return M + (long long)(NMASK + 1) * d.Wtot + (long long)b * d.OW; }
@@ -2492,7 +2486,7 @@ __device__ void load_instance(TeamSmem<T> &sm, const InstDesc &dg, int tid) {
         }
         sm.woff[Jmax + 1] = o;
         sm.ooff[Jmax + 1] = oo;
-        sm.sparse = (SPM == 2 || (SPM == 1 && dg.Wtot >= CW_MIN_WORDS)) ? 1 : 0;
+        sm.sparse = SPM != 0 ? 1 : 0;
         // without candidate words every word of level l is visited
         if (!sm.sparse)
             for (int l = Jmin; l <= Jmax + 1; ++l) sm.cw_seg[l] = sm.woff[l];
@@ -2575,7 +2569,7 @@ __device__ void run_team(TeamSmem<T> &sm, const Tables<T> &tab, BlockScratch &bx
     const bool local = smask != nullptr && region <= cap;
     uint32_t *masks = local ? smask : sm.d.masks;
     const long long oo = (long long)(NMASK + 1) * W + (long long)sm.cur * OW;  // occupancy of the current tree
-    if (SPM == 2 || (SPM == 1 && sm.sparse)) {
+    if constexpr (SPM != 0) {
         // the other tree buffer starts empty: a step writes its new tree there in candidate words only
         uint32_t *other = masks + (long long)(sm.cur ^ 1) * W;
         for (int g = tid; g < W; g += TS) other[g] = 0u;
@@ -2589,7 +2583,7 @@ __device__ void run_team(TeamSmem<T> &sm, const Tables<T> &tab, BlockScratch &bx
             smask[M_PRED * W + g] = gp[g];
             smask[M_GH * W + g] = gg[g];
         }
-        if (SPM == 2 || (SPM == 1 && sm.sparse))
+        if constexpr (SPM != 0)
             for (int g = tid; g < OW; g += TS) smask[oo + g] = sm.d.masks[oo + g];
     }
     __syncthreads();
@@ -2616,7 +2610,7 @@ __device__ void run_team(TeamSmem<T> &sm, const Tables<T> &tab, BlockScratch &bx
             gg[g] = smask[M_GH * W + g];
         }
         const long long oc = (long long)(NMASK + 1) * W + (long long)sm.cur * OW;
-        if (SPM == 2 || (SPM == 1 && sm.sparse))
+        if constexpr (SPM != 0)
             for (int g = tid; g < OW; g += TS) sm.d.masks[oc + g] = smask[oc + g];
     }
     store_instance<T, TS>(sm, tid);
@@ -2625,14 +2619,16 @@ __device__ void run_team(TeamSmem<T> &sm, const Tables<T> &tab, BlockScratch &bx
 // Persistent kernel: each block takes instances from the queue (largest first)
 // and advances one at a time with all its threads.  KIND selects the code the
 // kernel holds: K_FAST every scheme with gamma = 1 and the leaves collision;
-// K_GENERAL and K_RECOLL wide prediction stencils (gamma = 2, 3) and the
-// reconstructed collision; K_SCALAR the gamma = 1 code of the scalar D1Q2
-// scheme alone, whose smaller register footprint lets more blocks share an SM
-// (a larger MINB).
+// K_LARGE the same schemes with the word passes over candidate words, for
+// instances of at least CW_MIN_WORDS words per bitmask; K_GENERAL and K_RECOLL
+// wide prediction stencils (gamma = 2, 3) and the reconstructed collision, at
+// any size with the word passes over every word; K_SCALAR the gamma = 1 code
+// of the scalar D1Q2 scheme alone, whose smaller register footprint lets more
+// blocks share an SM (a larger MINB).
 template <typename T, int NT, int MINB, int KIND>
 __global__ void __launch_bounds__(NT, MINB) mr_persistent(LaunchArgs a) {
     constexpr bool WIDE = KIND == K_GENERAL || KIND == K_RECOLL;
-    constexpr int SPM = KIND == K_LARGE ? 2 : WIDE ? 1 : 0;
+    constexpr int SPM = KIND == K_LARGE ? 1 : 0;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     BlockSmem<T, NT> &bs = *reinterpret_cast<BlockSmem<T, NT> *>(smem_raw);
     uint32_t *smask = a.smem_mask_words > 0

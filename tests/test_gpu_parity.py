@@ -493,6 +493,8 @@ GAMMA_CASES = [
     ("g3-adv-periodic", lambda: W.random_smooth(10, W.EQ_ADVECTION, seed=73, eps=1e-4).with_(gamma=3)),
     ("g3-euler-jmin4", lambda: W.random_smooth(9, W.EQ_EULER, seed=74, eps=1e-4, Jmin=4, bc=W.BC_COPY).with_(gamma=3)),
     ("g2-testIV", lambda: W.scalar_test("IV").with_(gamma=2)),
+    # 4096 words per bitmask: a large instance in the general variant (every word visited)
+    ("g2-burgers-J15", lambda: W.random_smooth(15, W.EQ_BURGERS, seed=76, eps=1e-4).with_(gamma=2)),
 ]
 
 
