@@ -87,6 +87,17 @@ def test_batch_creation_checks_every_descriptor():
     buf = ctypes.create_string_buffer(256)
     L.mr_last_error(None, buf, 256)
     assert b"instance 2" in buf.value
+    # the lattice velocity lambda is taken in [2^-16, 2^16], where the FP64
+    # collision's division by a lambda that is no power of two (Markstein's
+    # correction) stays away from overflow and underflow
+    descs[2].s[0] = 1.0
+    for lam, ok in ((2.0 ** 16, True), (3.0 * 2.0 ** -16, True), (2.0 ** -16, True),
+                    (2.0 ** 16 * 1.5, False), (2.0 ** -17, False), (0.0, False), (float("nan"), False)):
+        descs[0].lambda_ = lam
+        rc = L.mr_batch_create(ctypes.byref(h), descs, 3, capi.MR_FP64)
+        assert rc == (capi.MR_OK if ok else capi.MR_ERR_ARG), lam
+        if ok:
+            L.mr_destroy(h)
 
 
 def _table(dj, kind):

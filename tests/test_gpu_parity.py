@@ -515,6 +515,25 @@ def test_wide_stencil_lockstep_parity(name, make):
         assert_same_leaves(lvs, o)
 
 
+@pytest.mark.parametrize("lam", [3.0 * 2.0 ** 14, 3.0 * 2.0 ** -15])
+def test_extreme_lattice_velocity_lockstep_parity(lam):
+    """A lattice velocity that is no power of two near either end of the
+    accepted range [2^-16, 2^16]: the FP64 collision's division by lambda
+    (Markstein's correction) gives the oracle's quotients, so meshes match bit
+    for bit and populations within 1e-12, step by step from identical states."""
+    inst = W.random_smooth(9, W.EQ_ADVECTION, seed=77, eps=1e-4).with_(lam=lam, eqp=0.25 * lam, s=(1.3,))
+    s = _solver(inst)
+    o = O.Oracle(params_of(inst))
+    for n in range(8):
+        R, vals, _ = gpu_state(s)
+        o.set_state(R, vals)
+        o.step()
+        s.advance(1)
+        R2, _, lvs = gpu_state(s)
+        assert np.array_equal(R2, o.get_state()[0]), f"step {n}: mesh differs"
+        assert_same_leaves(lvs, o)
+
+
 @pytest.mark.parametrize("name,make", GAMMA_CASES, ids=[c[0] for c in GAMMA_CASES])
 def test_wide_stencil_free_running_parity(name, make):
     inst = make()
