@@ -20,7 +20,10 @@ BUILD = os.path.join(HERE, "_build")
 
 NVCC = os.environ.get("NVCC", "nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", f"-I{INCLUDE}"]
+# host code without fused multiply-add contraction (GCC contracts by default on
+# aarch64, not on x86-64), so host-computed constants (M^-1 of the D1Q3 / D1Q5
+# schemes, the scheme constants) are the same on both machines
+FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-ffp-contract=off", f"-I{INCLUDE}"]
 
 
 def _sources() -> list[str]:
