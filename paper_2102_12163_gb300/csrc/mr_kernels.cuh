@@ -193,7 +193,7 @@ struct TeamSmem {
 // block-team scratch (scan partials and reduction slots of the warps)
 struct BlockScratch {
     int scan_w[2][NLIST][32];
-    double red[3][32];
+    double red[3][64];
 };
 
 template <typename T, int NT>
@@ -670,25 +670,39 @@ struct Worker {
     __device__ __forceinline__ SRow<T, q> phi(int h) const { return SRow<T, q>{Phi + h}; }
 
     // sums over the team of nf per-thread doubles, valid in thread 0 (one barrier)
+    // The team's sum of x[j], in thread 0.  GB300's FP64 units take a warp-wide
+    // instruction whole whatever its active lanes, so the additions are kept
+    // off most warps: a few shuffle rounds in each warp leave 64 partial sums
+    // per field (groups of TS / 64 lanes) in shared memory, and warp 0 folds
+    // them (two per lane, then a shuffle tree).  A fixed order: deterministic.
     __device__ __forceinline__ void team_sum(double (&x)[3]) {
+        if constexpr (WARP) {
 #pragma unroll
-        for (int j = 0; j < 3; ++j)
-            if (j < nf)
+            for (int j = 0; j < 3; ++j)
+                if (j < nf)
 #pragma unroll
-                for (int o = 16; o > 0; o >>= 1) x[j] += __shfl_down_sync(FULL, x[j], o);
-        if constexpr (!WARP) {
-            if ((tid & 31) == 0)
+                    for (int o = 16; o > 0; o >>= 1) x[j] += __shfl_down_sync(FULL, x[j], o);
+        } else {
+            static_assert(TS >= 64 && TS % 64 == 0, "team width");
+            constexpr int G = TS / 64;  // lanes per partial sum: 1, 2, 4, 8 or 16
+#pragma unroll
+            for (int j = 0; j < 3; ++j)
+                if (j < nf)
+#pragma unroll
+                    for (int o = G / 2; o > 0; o >>= 1) x[j] += __shfl_down_sync(FULL, x[j], o);
+            if ((tid & (G - 1)) == 0)
 #pragma unroll
                 for (int j = 0; j < 3; ++j)
-                    if (j < nf) bx.red[j][tid >> 5] = x[j];
+                    if (j < nf) bx.red[j][tid / G] = x[j];
             sync();
-            if (tid == 0)
+            if (tid < 32)
 #pragma unroll
                 for (int j = 0; j < 3; ++j)
                     if (j < nf) {
-                        double t = 0.0;
-                        for (int w = 0; w < TS / 32; ++w) t += bx.red[j][w];
-                        x[j] = t;
+                        double v = bx.red[j][tid] + bx.red[j][tid + 32];
+#pragma unroll
+                        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(FULL, v, o);
+                        x[j] = v;
                     }
         }
     }
