@@ -1325,11 +1325,14 @@ struct Worker {
     // reloaded after the previous level wrote them.
     __device__ void small_levels(uint32_t *Rn, const uint32_t *Ro, bool grade) {
         const int gam = WIDE ? d.gamma : 1;
+        // the descriptor fields in registers: a store through a mask pointer
+        // could otherwise force their reload from shared memory at every level
+        const int Jmin = d.Jmin, Jmax = d.Jmax, bc = d.bc;
         uint32_t *LF = mask(M_LEAF), *PR = mask(M_PRED), *GH = mask(M_GH);
-        const int ltop = d.Jmax < 5 ? d.Jmax : 5;
+        const int ltop = Jmax < 5 ? Jmax : 5;
         // words of level ltop + 1 (two words when it has 64 cells, one when fewer)
         uint32_t rc0 = 0u, rc1 = 0u, pc0 = 0u, pc1 = 0u, gc0 = 0u, gc1 = 0u;
-        if (ltop < d.Jmax) {
+        if (ltop < Jmax) {
             const int oc = sm.woff[ltop + 1];
             rc0 = Rn[oc];
             pc0 = PR[oc];
@@ -1341,21 +1344,23 @@ struct Worker {
             }
         }
         uint32_t r = Rn[sm.woff[ltop]];
-        for (int l = ltop; l >= d.Jmin; --l) {
-            const int n = 1 << l, o = sm.woff[l];
+        int o = sm.woff[ltop];
+        for (int l = ltop; l >= Jmin; --l) {
+            const int n = 1 << l;
+            const int op = l > Jmin ? sm.woff[l - 1] : 0;
             const uint32_t vb = n == 32 ? 0xFFFFFFFFu : ((1u << n) - 1u);
             const uint32_t ro = Ro[o];
-            uint32_t rp = l > d.Jmin ? Rn[sm.woff[l - 1]] : 0u;
-            if (grade && l > d.Jmin + 1) {
+            uint32_t rp = l > Jmin ? Rn[op] : 0u;
+            if (grade && l > Jmin + 1) {
                 const int np = n >> 1;
                 const uint32_t vbp = (1u << np) - 1u;
-                rp |= pairexpand(dil_small(fold2(r, 0u), np, gam)) & vbp;
+                rp |= pairexpand(dil_small(fold2(r, 0u), np, gam, bc)) & vbp;
             }
             uint32_t lf = r, pr, gh = 0u;
-            if (l < d.Jmax) {
+            if (l < Jmax) {
                 lf = r & ~fold2(rc0, rc1);
-                pr = (lf | dil_small(fold2(pc0, pc1), n, gam)) & ~ro;
-                gh = (dil_small(lf, n, 2 * gam) | dil_small(fold2(gc0, gc1), n, gam)) & ~r;
+                pr = (lf | dil_small(fold2(pc0, pc1), n, gam, bc)) & ~ro;
+                gh = (dil_small(lf, n, 2 * gam, bc) | dil_small(fold2(gc0, gc1), n, gam, bc)) & ~r;
             } else {
                 pr = lf & ~ro;
             }
@@ -1365,7 +1370,7 @@ struct Worker {
             LF[o] = lf;
             PR[o] = pr;
             GH[o] = gh;
-            if (l > d.Jmin) Rn[sm.woff[l - 1]] = rp;
+            if (l > Jmin) Rn[op] = rp;
             rc0 = r;
             rc1 = 0u;
             pc0 = pr;
@@ -1373,15 +1378,16 @@ struct Worker {
             gc0 = gh;
             gc1 = 0u;
             r = rp;
+            o = op;
         }
     }
 
     // dilation by r cells inside a level of n <= 32 cells held in one word
-    __device__ __forceinline__ uint32_t dil_small(uint32_t x, int n, int r) const {
+    __device__ __forceinline__ uint32_t dil_small(uint32_t x, int n, int r, int bc) const {
         const uint32_t vb = n == 32 ? 0xFFFFFFFFu : ((1u << n) - 1u);
         uint32_t out = x;
         for (int s = 1; s <= r; ++s) {
-            if (d.bc == 0) {
+            if (bc == 0) {
                 // rotations within the level (a wide stencil's reach may exceed n)
                 const int sm_ = WIDE ? s % n : s;
                 if (sm_) out |= ((x << sm_) | (x >> (n - sm_)) | (x >> sm_) | (x << (n - sm_))) & vb;
