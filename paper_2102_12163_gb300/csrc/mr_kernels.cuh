@@ -609,14 +609,16 @@ struct Worker {
     const InstDesc &d;
     T *V;
     T *Phi;
-    uint32_t *M;  // mask base (shared memory when the masks fit, else global)
-    int tid;      // rank in the team
+    uint32_t *M;     // mask base (shared memory when the masks fit, else global)
+    int tid;         // rank in the team
+    long long voff;  // -2^Jmin q: level l's values start at V + 2^l q + voff
 
     __device__ Worker(TeamSmem<T> &s, const Tables<T> &tb, BlockScratch &x, int rank, uint32_t *masks)
         : sm(s), tab(tb), bx(x), d(s.d), tid(rank) {
         V = (T *)d.V;
         Phi = (T *)d.Phi;
         M = masks;
+        voff = -(1LL << d.Jmin) * q;
     }
 
     // leaves collision of the q populations of one cell
@@ -666,7 +668,17 @@ struct Worker {
     __device__ __forceinline__ uint32_t *occ(int b) { return M + (long long)(NMASK + 1) * d.Wtot + (long long)b * d.OW; }
     __device__ __forceinline__ uint32_t *list(int L) { return d.lists + d.list_off[L]; }
     // population h on level l, and population h of the interface array
-    __device__ __forceinline__ SRow<T, q> row(int h, int l) const { return SRow<T, q>{V + cell_off(l, d.Jmin) * q + h}; }
+    // population h of level l, at cell_off(l, Jmin) q + h.  The FP64 kernels hold
+    // Jmin in voff: the descriptor field, reloaded from shared memory after every
+    // store, would sit on the dependent chain of each population loop (measured:
+    // +1.5 % FP64); the FP32 kernels keep the reload, whose register is dearer
+    // to them (the offset cost them spills and 3.6 %)
+    __device__ __forceinline__ SRow<T, q> row(int h, int l) const {
+        if constexpr (sizeof(T) == 8)
+            return SRow<T, q>{V + ((1LL << l) * q + voff + h)};
+        else
+            return SRow<T, q>{V + cell_off(l, d.Jmin) * q + h};
+    }
     __device__ __forceinline__ SRow<T, q> phi(int h) const { return SRow<T, q>{Phi + h}; }
 
     // sums over the team of nf per-thread doubles, valid in thread 0 (one barrier)
